@@ -1,0 +1,253 @@
+"""GB300-native block LOBPCG for a sparse symmetric matrix stored as one triangle.
+
+Thin ctypes binding over the C ABI declared in ``include/lobpcg.h``: the
+functions and methods here only marshal arguments; every step of the
+computation runs in the CUDA kernels of ``liblobpcg.so``.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is not
+built, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+LOBPCG_OK = 0
+STATUS = {
+    0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN", 5: "ERR_NONFINITE",
+    6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_BOUNDS", 9: "ERR_UNSUPPORTED",
+}
+MEM_DEVICE, MEM_HOST = 0, 1
+PRECOND = {"none": 0, "diag": 1, "bjacobi": 2, "mlp": 3}
+
+
+class LobpcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Matrix(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("val_is_fp64", ctypes.c_int32),
+                ("mem", ctypes.c_int32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("nev", ctypes.c_int32), ("maxiter", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("precond", ctypes.c_int32), ("resid_mode", ctypes.c_int32),
+                ("polish_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_blocks", ctypes.c_int64),
+                ("chunks", ctypes.c_int64), ("padded_nnz", ctypes.c_int64), ("full_chunks", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("gershgorin", ctypes.c_double), ("num_sms", ctypes.c_int32),
+                ("warps", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load():
+    """Load ``liblobpcg.so``; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.SO):
+        raise ImportError(f"{_build.SO} is missing: run __graft_entry__.build() (or python -m "
+                          "paper_2109_00485_gb300._build) first; there is no CPU fallback")
+    L = ctypes.CDLL(_build.SO)
+    vp, i32, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
+    L.lobpcg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Matrix), ctypes.POINTER(_Params), vp]
+    L.lobpcg_create.restype = st
+    L.lobpcg_destroy.argtypes = [vp]
+    L.lobpcg_destroy.restype = st
+    L.lobpcg_last_error.argtypes = [vp]
+    L.lobpcg_last_error.restype = ctypes.c_char_p
+    L.lobpcg_matrix_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.lobpcg_matrix_info.restype = st
+    L.lobpcg_sync.argtypes = [vp]
+    L.lobpcg_sync.restype = st
+    L.lobpcg_spmm_sym.argtypes = [vp, vp, vp, i32]
+    L.lobpcg_spmm_sym.restype = st
+    L.lobpcg_spmm_sym_f64.argtypes = [vp, vp, vp, i32]
+    L.lobpcg_spmm_sym_f64.restype = st
+    _lib = L
+    return L
+
+
+def _check(h, status):
+    if status != LOBPCG_OK:
+        msg = load().lobpcg_last_error(h)
+        raise LobpcgError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int:
+    """Data pointer of a torch tensor or numpy array."""
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _dev_block(t, dtype_name: str, n: int, k: int):
+    import torch
+    want = {"f32": torch.float32, "f64": torch.float64}[dtype_name]
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != want or t.shape != (n, k) or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {want} tensor of shape ({n}, {k}), got {t.dtype} {tuple(t.shape)}")
+
+
+class Handle:
+    """A created lobpcg handle (``lobpcg_create``)."""
+
+    def __init__(self, ptr: int, n: int, params: _Params, stream, keep=()):
+        self._h = ctypes.c_void_p(ptr)
+        self.n = n
+        self.params = params
+        self.stream = stream
+        self._keep = keep
+
+    # -- C ABI entry points ------------------------------------------------
+    def lobpcg_spmm_sym(self, X, Y=None, k: int | None = None):
+        """Y = H X (float32, device tensors n x k row-major)."""
+        import torch
+        k = X.shape[1] if k is None else k
+        _dev_block(X, "f32", self.n, k)
+        if Y is None:
+            Y = torch.empty_like(X)
+        _dev_block(Y, "f32", self.n, k)
+        _check(self._h, load().lobpcg_spmm_sym(self._h, _ptr(X), _ptr(Y), k))
+        return Y
+
+    def spmm_sym_host(self, Xh, Yh):
+        """``lobpcg_spmm_sym`` with HOST X and Y (pinned torch CPU tensors or
+        numpy arrays, float32 n x k); Y is valid after ``sync()``."""
+        for t in (Xh, Yh):
+            shape, ok = tuple(t.shape), (t.dtype == np.float32 if isinstance(t, np.ndarray) else str(t.dtype) == "torch.float32")
+            if shape[0] != self.n or len(shape) != 2 or not ok:
+                raise ValueError("host blocks must be float32 (n, k)")
+        k = Xh.shape[1]
+        _check(self._h, load().lobpcg_spmm_sym(self._h, _ptr(Xh), _ptr(Yh), k))
+        return Yh
+
+    def lobpcg_spmm_sym_f64(self, X, Y=None, k: int | None = None):
+        """Y = H X with float64 vectors and accumulation."""
+        import torch
+        k = X.shape[1] if k is None else k
+        _dev_block(X, "f64", self.n, k)
+        if Y is None:
+            Y = torch.empty_like(X)
+        _dev_block(Y, "f64", self.n, k)
+        _check(self._h, load().lobpcg_spmm_sym_f64(self._h, _ptr(X), _ptr(Y), k))
+        return Y
+
+    def lobpcg_sync(self):
+        _check(self._h, load().lobpcg_sync(self._h))
+
+    def lobpcg_matrix_info(self) -> dict:
+        info = _Info()
+        _check(self._h, load().lobpcg_matrix_info(self._h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in _Info._fields_}
+
+    def lobpcg_last_error(self) -> str:
+        msg = load().lobpcg_last_error(self._h)
+        return msg.decode() if msg else ""
+
+    def lobpcg_destroy(self):
+        if self._h:
+            load().lobpcg_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    # -- conveniences with the same meaning ---------------------------------
+    spmm_sym = lobpcg_spmm_sym
+    spmm_sym_f64 = lobpcg_spmm_sym_f64
+    sync = lobpcg_sync
+    info = lobpcg_matrix_info
+    destroy = lobpcg_destroy
+
+    def __del__(self):
+        try:
+            self.lobpcg_destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.lobpcg_destroy()
+
+
+def lobpcg_last_error() -> str:
+    """Text of the last failed ``lobpcg_create`` on this thread."""
+    msg = load().lobpcg_last_error(None)
+    return msg.decode() if msg else ""
+
+
+def make_params(k: int, nev: int | None = None, maxiter: int = 1000, tol: float = 1e-6, precond="diag",
+                resid_mode: int = 0, polish_fp64: int = 1, seed: int = 0) -> _Params:
+    p = _Params()
+    p.k = k
+    p.nev = k if nev is None else nev
+    p.maxiter = maxiter
+    p.tol = tol
+    p.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+    p.resid_mode = resid_mode
+    p.polish_fp64 = polish_fp64
+    p.seed = seed & (2 ** 64 - 1)
+    return p
+
+
+def lobpcg_create(n: int, row_ptr, col, val, params: _Params | None = None, stream=None, **kw) -> Handle:
+    """Create a handle from a lower-triangle CSR.
+
+    ``row_ptr`` (int64[n+1]), ``col`` (int32[nnz]) and ``val`` (float32 or
+    float64[nnz]) are either all numpy arrays (host) or all CUDA tensors.
+    ``stream`` is a ``torch.cuda.Stream`` (default: the current stream)."""
+    import torch
+    L = load()
+    if params is None:
+        params = make_params(**kw)
+    m = _Matrix()
+    m.n = int(n)
+    if isinstance(row_ptr, np.ndarray):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        if val.dtype not in (np.float32, np.float64):
+            raise TypeError("val must be float32 or float64")
+        val = np.ascontiguousarray(val)
+        m.mem = MEM_HOST
+        m.val_is_fp64 = 1 if val.dtype == np.float64 else 0
+        m.nnz = int(col.size)
+    else:
+        for t, dt in ((row_ptr, torch.int64), (col, torch.int32)):
+            if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+                raise TypeError("device CSR: row_ptr int64, col int32, contiguous CUDA tensors")
+        if val.dtype not in (torch.float32, torch.float64) or not val.is_cuda or not val.is_contiguous():
+            raise TypeError("val must be a contiguous CUDA float32/float64 tensor")
+        m.mem = MEM_DEVICE
+        m.val_is_fp64 = 1 if val.dtype == torch.float64 else 0
+        m.nnz = int(col.numel())
+    m.row_ptr, m.col, m.val = _ptr(row_ptr), _ptr(col), _ptr(val)
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream if stream is not None else 0
+    out = ctypes.c_void_p(0)
+    st = L.lobpcg_create(ctypes.byref(out), ctypes.byref(m), ctypes.byref(params), ctypes.c_void_p(sh))
+    if st != LOBPCG_OK:
+        msg = L.lobpcg_last_error(None)
+        raise LobpcgError(st, msg.decode() if msg else "")
+    return Handle(out.value, int(n), params, stream)
+
+
+def from_csr(A, params: _Params | None = None, stream=None, **kw) -> Handle:
+    """``lobpcg_create`` from an object with ``n, row_ptr, col, val`` (host arrays)."""
+    return lobpcg_create(A.n, A.row_ptr, A.col, A.val, params=params, stream=stream, **kw)

@@ -1,0 +1,226 @@
+// C ABI: handle lifetime, argument checks and dispatch to the kernels.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "internal.h"
+#include "lobpcg.h"
+
+using namespace lobpcg;
+
+namespace {
+thread_local std::string g_create_error;
+
+lobpcg_status fail(lobpcg_ctx *h, lobpcg_status st, const std::string &msg) {
+    if (h) h->last_error = msg; else g_create_error = msg;
+    return st;
+}
+
+lobpcg_status cuda_fail(lobpcg_ctx *h, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LOBPCG_ERR_OOM : LOBPCG_ERR_CUDA, msg);
+}
+
+void release(lobpcg_ctx *h) {
+    if (!h) return;
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->stage_x) cudaFree(h->stage_x);
+    if (h->stage_y) cudaFree(h->stage_y);
+    h->stage_x = h->stage_y = nullptr;
+    if (h->h_err) cudaFreeHost(h->h_err);
+    h->h_err = nullptr;
+}
+
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+}  // namespace
+
+namespace lobpcg {
+cudaError_t dev_alloc(lobpcg_ctx *h, void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(*p);
+    h->device_bytes += static_cast<int64_t>(bytes);
+    return cudaSuccess;
+}
+}  // namespace lobpcg
+
+extern "C" {
+
+lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_params *params, void *stream) {
+    if (!out) return fail(nullptr, LOBPCG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A || !params) return fail(nullptr, LOBPCG_ERR_ARG, "matrix or params is NULL");
+    if (A->n < 1 || A->n >= (int64_t(1) << 28)) return fail(nullptr, LOBPCG_ERR_ARG, "n must be in [1, 2^28)");
+    if (A->nnz < 0 || A->nnz >= (int64_t(1) << 40)) return fail(nullptr, LOBPCG_ERR_ARG, "nnz out of range");
+    if (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
+        return fail(nullptr, LOBPCG_ERR_ARG, "row_ptr/col/val is NULL");
+    if (A->mem != LOBPCG_MEM_DEVICE && A->mem != LOBPCG_MEM_HOST)
+        return fail(nullptr, LOBPCG_ERR_ARG, "mem must be LOBPCG_MEM_DEVICE or LOBPCG_MEM_HOST");
+    const lobpcg_params &P = *params;
+    if (P.k < 1 || P.k > 32) return fail(nullptr, LOBPCG_ERR_ARG, "k must be in [1, 32]");
+    if (P.nev < 1 || P.nev > P.k) return fail(nullptr, LOBPCG_ERR_ARG, "nev must be in [1, k]");
+
+    lobpcg_ctx *h = new (std::nothrow) lobpcg_ctx();
+    if (!h) return fail(nullptr, LOBPCG_ERR_OOM, "host allocation failed");
+    h->params = P;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->T.n = A->n;
+    h->T.nnz = A->nnz;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        lobpcg_status st = cuda_fail(nullptr, e, "device query");
+        delete h;
+        return st;
+    }
+    auto bail = [&](lobpcg_status st, const std::string &msg) {
+        g_create_error = msg;
+        release(h);
+        delete h;
+        return st;
+    };
+    e = dev_alloc(h, reinterpret_cast<void **>(&h->d_err), sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_err), sizeof(int) * 4);
+    if (e != cudaSuccess) return bail(LOBPCG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));
+
+    // Bring the CSR onto the device if it is on the host.
+    const size_t vsz = A->val_is_fp64 ? 8 : 4;
+    const int64_t *rp = A->row_ptr;
+    const int32_t *cl = A->col;
+    const void *vl = A->val;
+    void *tmp = nullptr;
+    if (A->mem == LOBPCG_MEM_HOST) {
+        const size_t b_rp = sizeof(int64_t) * (A->n + 1), b_cl = sizeof(int32_t) * A->nnz, b_vl = vsz * A->nnz;
+        const size_t o_cl = (b_rp + 255) & ~size_t(255), o_vl = (o_cl + b_cl + 255) & ~size_t(255);
+        e = cudaMallocAsync(&tmp, o_vl + b_vl + 16, h->stream);
+        if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? LOBPCG_ERR_OOM : LOBPCG_ERR_CUDA,
+                                          std::string("staging: ") + cudaGetErrorString(e));
+        char *base = static_cast<char *>(tmp);
+        e = cudaMemcpyAsync(base, A->row_ptr, b_rp, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && b_cl) e = cudaMemcpyAsync(base + o_cl, A->col, b_cl, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && b_vl) e = cudaMemcpyAsync(base + o_vl, A->val, b_vl, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, h->stream);
+            return bail(LOBPCG_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+        }
+        rp = reinterpret_cast<const int64_t *>(base);
+        cl = reinterpret_cast<const int32_t *>(base + o_cl);
+        vl = base + o_vl;
+    }
+    std::string err;
+    lobpcg_status st = LOBPCG_ERR_CUDA;
+    e = build_tiled(h, rp, cl, vl, A->val_is_fp64 != 0, err, st);
+    if (tmp) {
+        cudaFreeAsync(tmp, h->stream);
+        cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess)
+        return bail(e == cudaErrorMemoryAllocation ? LOBPCG_ERR_OOM : LOBPCG_ERR_CUDA,
+                    std::string("tiling: ") + cudaGetErrorString(e));
+    if (st != LOBPCG_OK) return bail(st, err);
+    *out = h;
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_destroy(lobpcg_t h) {
+    if (!h) return LOBPCG_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return LOBPCG_OK;
+}
+
+const char *lobpcg_last_error(lobpcg_t h) {
+    return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+lobpcg_status lobpcg_matrix_info(lobpcg_t h, lobpcg_info *info) {
+    if (!h || !info) return LOBPCG_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n = h->T.n;
+    info->nnz = h->T.nnz;
+    info->row_blocks = h->T.R;
+    info->chunks = h->T.nchunks;
+    info->padded_nnz = h->T.npad;
+    info->full_chunks = h->T.full_chunks;
+    info->device_bytes = h->device_bytes;
+    info->gershgorin = h->gershgorin;
+    info->num_sms = h->num_sms;
+    info->warps = h->T.warps;
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_sync(lobpcg_t h) {
+    if (!h) return LOBPCG_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    if (*h->h_err == DEV_TIMEOUT) {
+        cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+        return fail(h, LOBPCG_ERR_TIMEOUT, "a device-side wait gave up (bulk copy did not complete)");
+    }
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_spmm_sym(lobpcg_t h, const float *X, float *Y, int32_t k) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!X || !Y) return fail(h, LOBPCG_ERR_ARG, "X or Y is NULL");
+    if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
+    const size_t bytes = sizeof(float) * static_cast<size_t>(h->T.n) * k;
+    if (ranges_overlap(X, bytes, Y, bytes)) return fail(h, LOBPCG_ERR_ARG, "X and Y overlap");
+    const bool xh = is_host_ptr(X), yh = is_host_ptr(Y);
+    if (xh != yh) return fail(h, LOBPCG_ERR_ARG, "X and Y must both be host or both be device pointers");
+    cudaError_t e;
+    if (xh) {
+        // host buffers: stage through the handle's device blocks
+        if (static_cast<size_t>(k) > h->stage_k) {
+            for (float **b : {&h->stage_x, &h->stage_y}) {
+                if (*b) { cudaFree(*b); h->device_bytes -= sizeof(float) * h->T.n * h->stage_k; }
+                *b = nullptr;
+            }
+            e = cudaMalloc(&h->stage_x, bytes);
+            if (e == cudaSuccess) e = cudaMalloc(&h->stage_y, bytes);
+            if (e != cudaSuccess) return cuda_fail(h, e, "staging");
+            h->stage_k = k;
+            h->device_bytes += 2 * static_cast<int64_t>(bytes);
+        }
+        e = cudaMemcpyAsync(h->stage_x, X, bytes, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_spmm_sym_f32(h, h->stage_x, h->stage_y, k, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Y, h->stage_y, bytes, cudaMemcpyDeviceToHost, h->stream);
+    } else {
+        e = launch_spmm_sym_f32(h, X, Y, k, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "spmm_sym");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double *Y, int32_t k) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!X || !Y) return fail(h, LOBPCG_ERR_ARG, "X or Y is NULL");
+    if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
+    const size_t bytes = sizeof(double) * static_cast<size_t>(h->T.n) * k;
+    if (ranges_overlap(X, bytes, Y, bytes)) return fail(h, LOBPCG_ERR_ARG, "X and Y overlap");
+    cudaError_t e = launch_spmm_sym_f64(h, X, Y, k, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "spmm_sym_f64");
+    return LOBPCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal state of a lobpcg handle and the launchers the C ABI calls.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "lobpcg.h"
+
+namespace lobpcg {
+
+// Tiled copy of the stored lower triangle.
+//
+// Rows are grouped in row blocks of 16.  Within a row block the entries are
+// grouped by 16-column tile ("chunks"); the diagonal chunk comes first, then
+// the off-diagonal chunks in ascending tile order.  Inside a chunk entries
+// keep CSR order (by row, then column), so a chunk holding all 256 entries of
+// its tile is exactly that tile in row-major order.  Each chunk is padded to
+// a multiple of 4 entries (16 bytes) so it can be moved by bulk copies.
+//   idx[e] = col | (row_in_block << 28), or IDX_PAD for padding
+//   val[e] = float32 value (0 for padding)
+//   chunk_off[c]   first entry of chunk c (chunk_off[nchunks] = padded nnz)
+//   chunk_ct[c]    column tile of chunk c (col >> 4)
+//   chunk_info[c]  real entry count | DIAG_FLAG for the diagonal chunk
+//   rb_chunk[rb]   first chunk of row block rb (rb_chunk[R] = nchunks)
+//   warp_rb[w]     first row block of SpMM warp w (warp_rb[W] = R)
+struct Tiled {
+    int64_t n = 0, nnz = 0, R = 0, nchunks = 0, npad = 0, full_chunks = 0;
+    uint32_t *idx = nullptr;
+    float *val = nullptr;
+    int64_t *chunk_off = nullptr;
+    int32_t *chunk_ct = nullptr;
+    int32_t *chunk_info = nullptr;
+    int64_t *rb_chunk = nullptr;
+    int32_t *warp_rb = nullptr;
+    int32_t warps = 0;
+    float *diag = nullptr;   // d_i = h_ii (float32)
+};
+
+}  // namespace lobpcg
+
+struct lobpcg_ctx {
+    lobpcg::Tiled T;
+    lobpcg_params params{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    double gershgorin = 0.0;
+    int *d_err = nullptr;        // device error word (DevErr)
+    int *h_err = nullptr;        // pinned mirror
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;  // every device allocation, freed at destroy
+    float *stage_x = nullptr;    // device staging of host X / Y blocks (spmm_sym with host pointers)
+    float *stage_y = nullptr;
+    size_t stage_k = 0;
+    std::string last_error;
+};
+
+namespace lobpcg {
+
+// tiling.cu
+cudaError_t build_tiled(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t *col, const void *val,
+                        bool val_fp64, std::string &err, lobpcg_status &st);
+
+// spmm_sym.cu
+cudaError_t launch_spmm_sym_f32(const lobpcg_ctx *h, const float *X, float *Y, int k, cudaStream_t s);
+cudaError_t launch_spmm_sym_f64(const lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s);
+
+// helpers in api.cu
+cudaError_t dev_alloc(lobpcg_ctx *h, void **p, size_t bytes);
+
+}  // namespace lobpcg

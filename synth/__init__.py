@@ -139,6 +139,8 @@ WORKLOADS = {
     "small_n20k": dict(n=20_000, nnz_per_row=100.0, k=8, nev=5, seed=1, fp32=False),
     "full_n2m": dict(n=2_000_000, nnz_per_row=400.0, k=16, nev=8, seed=2, fp32=True),
     "largest_n8m": dict(n=8_000_000, nnz_per_row=250.0, k=20, nev=10, seed=5, fp32=True),
+    # same structure at a quarter of the rows: ~1.6 GB, still far larger than L2 (profiling captures)
+    "profile_n500k": dict(n=500_000, nnz_per_row=400.0, k=16, nev=8, seed=3, fp32=True),
 }
 X0_SEED_OFFSET = 1000
 
