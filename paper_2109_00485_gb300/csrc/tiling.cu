@@ -157,7 +157,7 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     // 1. validate
     int *d_bad = nullptr;
     unsigned long long *d_bad_row = nullptr, *d_gmax = nullptr;
-    TRY(cudaMallocAsync(&d_bad, sizeof(int) + 2 * sizeof(unsigned long long), s));
+    TRY(cudaMallocAsync(&d_bad, 32, s));  // flag at 0, bad row at 8, Gershgorin bits at 16
     d_bad_row = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(d_bad) + 8);
     d_gmax = d_bad_row + 1;
     // zero flag, set bad_row to max, zero gmax
