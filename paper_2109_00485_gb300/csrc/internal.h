@@ -8,6 +8,14 @@
 
 namespace lobpcg {
 
+// One 16-byte record per chunk (see Tiled).
+struct __align__(16) ChunkRec {
+    int64_t off;
+    int32_t ct;
+    int32_t info;
+};
+constexpr int NPAD_SHIFT = 20;
+
 // Tiled copy of the stored lower triangle.
 //
 // Rows are grouped in row blocks of 16.  Within a row block the entries are
@@ -15,21 +23,21 @@ namespace lobpcg {
 // the off-diagonal chunks in ascending tile order.  Inside a chunk entries
 // keep CSR order (by row, then column), so a chunk holding all 256 entries of
 // its tile is exactly that tile in row-major order.  Each chunk is padded to
-// a multiple of 4 entries (16 bytes) so it can be moved by bulk copies.
-//   idx[e] = col | (row_in_block << 28), or IDX_PAD for padding
-//   val[e] = float32 value (0 for padding)
-//   chunk_off[c]   first entry of chunk c (chunk_off[nchunks] = padded nnz)
-//   chunk_ct[c]    column tile of chunk c (col >> 4)
-//   chunk_info[c]  real entry count | DIAG_FLAG for the diagonal chunk
+// a multiple of 4 entries (16 bytes) and stored as one contiguous run of
+// 2 npad words -- its npad index words, then its npad value words -- so one
+// bulk copy moves a whole chunk.
+//   index word = col | (row_in_block << 28), or IDX_PAD for padding
+//   value word = float32 bits (0 for padding)
+//   chunk[c].off   first (padded) entry of chunk c; its words start at
+//                  data[2 chunk[c].off]
+//   chunk[c].ct    column tile of chunk c (col >> 4)
+//   chunk[c].info  real entry count | DIAG_FLAG (diagonal chunk) | npad << 20
 //   rb_chunk[rb]   first chunk of row block rb (rb_chunk[R] = nchunks)
 //   warp_rb[w]     first row block of SpMM warp w (warp_rb[W] = R)
 struct Tiled {
     int64_t n = 0, nnz = 0, R = 0, nchunks = 0, npad = 0, full_chunks = 0;
-    uint32_t *idx = nullptr;
-    float *val = nullptr;
-    int64_t *chunk_off = nullptr;
-    int32_t *chunk_ct = nullptr;
-    int32_t *chunk_info = nullptr;
+    uint32_t *data = nullptr;
+    struct ChunkRec *chunk = nullptr;
     int64_t *rb_chunk = nullptr;
     int32_t *warp_rb = nullptr;
     int32_t warps = 0;

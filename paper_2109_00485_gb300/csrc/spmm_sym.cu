@@ -6,16 +6,19 @@
 // MPI; on one GPU both are applied while the entry sits in shared memory.
 //
 // Work unit: one "chunk" = the entries of one row block (16 rows) that fall
-// in one 16-column tile, streamed HBM -> shared memory by bulk (TMA) copies
-// together with the 16 rows of X the tile's columns select.  Per chunk a
-// warp forms the 16x16 tile H_t (dense, zero-filled when partial) and its
-// transpose in shared memory, then
-//     Y_R += H_t X_C     (rows of this row block; kept in registers)
-//     Y_C  = H_t^T X_R   (rows of the tile's columns; vector atomics to L2)
-// X_R (this row block's 16 rows of X) is held in registers for the row
-// block.  The diagonal chunk is expanded to the symmetric tile S = L + L^T - D
-// and applied as Y_R += S X_R.  Y_R is flushed once per row block with
-// vector atomics, since other warps add transposed parts to the same rows.
+// in one 16-column tile.  One bulk (TMA) copy streams the chunk (indices and
+// values) HBM -> shared memory, a second brings the 16 rows of X the tile's
+// columns select.  The warp scatters the entries into the dense 16x16 tile
+// H_t and its transpose (zero-filled when the chunk is partial), then
+//     Y_R += H_t X_C    (this row block's rows; accumulated over its chunks)
+//     Y_C  = H_t^T X_R  (the tile's column rows; added to Y by a bulk reduce)
+// Both are 16x16x16 products on the tensor cores (mma.sync m16n8k8, TF32).
+// FP32 accuracy comes from the 3-term split a = a_hi + a_lo (a_hi = tf32(a),
+// a_lo = tf32(a - a_hi)): a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
+// accumulation.  X_R (this row block's 16 rows of X) stays in registers as
+// split B fragments.  The diagonal chunk is expanded to S = L + L^T - D and
+// applied as Y_R += S X_R.  Y_R of a row block is added to Y by a bulk
+// reduce too, since other warps add transposed parts to the same rows.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -24,34 +27,45 @@
 
 namespace lobpcg {
 
-template <int K>
+// Pipeline depth and residency (tunable at build time; the row-block
+// partition made at create assumes SPMM_WARPS_PER_SM resident warps).
+#ifndef SPMM_STAGES
+#define SPMM_STAGES 3
+#endif
+#ifndef SPMM_WARPS
+#define SPMM_WARPS 8
+#endif
+#ifndef SPMM_MINB
+#define SPMM_MINB 2
+#endif
+
+constexpr int HS = 20;   // row stride of the scattered tiles: fragment loads are bank-conflict free
+
+// NT = number of 8-column n-tiles of the vector block (k <= 8 NT).
+template <int NT>
 struct SpmmCfg {
-    static constexpr int GK = K / 4;      // lanes along k (groups of 4 columns)
-    static constexpr int RPL = K / 8;     // rows (and tile columns) per lane
-    static constexpr int STAGES = 3;
-    static constexpr int WARPS = 8;
-    static constexpr int MINB = (K <= 16) ? 2 : 1;
+    static constexpr int K = 8 * NT;
+    static constexpr int STAGES = SPMM_STAGES;
+    static constexpr int WARPS = SPMM_WARPS;
+    static constexpr int MINB = SPMM_MINB;
 };
 
-template <int K>
+template <int NT>
 struct __align__(16) WarpSmem {
-    float vals[SpmmCfg<K>::STAGES][256];
-    uint32_t idx[SpmmCfg<K>::STAGES][256];
-    float xt[SpmmCfg<K>::STAGES][TILE * K];
-    float H[256];         // row-major tile for partially filled chunks
-    float HT[TILE * 18];  // transposed tile (stride 18: conflict-free scatter and pair loads)
-    int4 meta[SpmmCfg<K>::STAGES];   // column tile, info, padded count, valid rows
-    uint64_t bar[SpmmCfg<K>::STAGES];
+    uint32_t cd[SpmmCfg<NT>::STAGES][512];        // one chunk: npad index words, then npad value words
+    float xt[SpmmCfg<NT>::STAGES][TILE * 8 * NT];  // X rows of the chunk's column tile (row stride k)
+    float yt[2][TILE * 8 * NT];                     // Y tiles handed to the bulk reduce (double-buffered)
+    float H[TILE * HS];                             // tile (or symmetric diagonal tile), row-major
+    float HT[TILE * HS];                            // transposed tile
+    int4 meta[SpmmCfg<NT>::STAGES];                 // column tile, info, padded count, valid rows
+    uint64_t bar[SpmmCfg<NT>::STAGES];
 };
 
 struct SpmmArgs {
     int64_t n;
     int k;
-    const uint32_t *idx;
-    const float *val;
-    const int64_t *chunk_off;
-    const int32_t *chunk_ct;
-    const int32_t *chunk_info;
+    const uint32_t *data;
+    const ChunkRec *chunk;
     const int64_t *rb_chunk;
     const int32_t *warp_rb;
     int W;
@@ -60,84 +74,139 @@ struct SpmmArgs {
     int *err;
 };
 
-template <int K>
-__device__ __forceinline__ void issue_chunk(const SpmmArgs &a, WarpSmem<K> *ws, int64_t c, int s,
-                                            uint64_t pol_stream, uint64_t pol_keep) {
-    const int64_t off = a.chunk_off[c];
-    const int npad = static_cast<int>(a.chunk_off[c + 1] - off);
-    const int ct = a.chunk_ct[c];
-    const int info = a.chunk_info[c];
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// d += a b  (m16n8k8, TF32 inputs, FP32 accumulate)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B with A, B given as (hi, lo) splits: three products, small first.
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+// A fragment (16x8 slice ks of a 16x16 tile stored row-major with stride HS):
+// a0 = T[g][8ks+t], a1 = T[g+8][8ks+t], a2 = T[g][8ks+t+4], a3 = T[g+8][8ks+t+4].
+__device__ __forceinline__ void load_a(const float *T, int ks, int g, int t, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+    const float *p = T + g * HS + 8 * ks + t;
+    split_tf32(p[0], ah[0], al[0]);
+    split_tf32(p[8 * HS], ah[1], al[1]);
+    split_tf32(p[4], ah[2], al[2]);
+    split_tf32(p[8 * HS + 4], ah[3], al[3]);
+}
+
+// Issue the bulk copies of one chunk into stage s (one lane).
+template <int NT>
+__device__ __forceinline__ void issue_chunk(const SpmmArgs &a, WarpSmem<NT> *ws, int4 rec, int s, uint64_t pol_stream,
+                                            uint64_t pol_keep) {
+    const int64_t off = static_cast<int64_t>((static_cast<uint64_t>(static_cast<uint32_t>(rec.y)) << 32) |
+                                             static_cast<uint32_t>(rec.x));
+    const int ct = rec.z, info = rec.w;
+    const int npad = (info >> NPAD_SHIFT) & 0x3FF;
     const int64_t r0 = static_cast<int64_t>(ct) * TILE;
     const int rows = static_cast<int>(a.n - r0 < TILE ? a.n - r0 : TILE);
     const uint32_t xbytes = static_cast<uint32_t>(rows) * a.k * 4u;
     ws->meta[s] = make_int4(ct, info, npad, rows);
     mbar_arrive_expect_tx(&ws->bar[s], static_cast<uint32_t>(npad) * 8u + xbytes);
-    if (npad > 0) {
-        bulk_g2s(ws->vals[s], a.val + off, npad * 4u, &ws->bar[s], pol_stream);
-        bulk_g2s(ws->idx[s], a.idx + off, npad * 4u, &ws->bar[s], pol_stream);
-    }
+    if (npad > 0) bulk_g2s(ws->cd[s], a.data + 2 * off, npad * 8u, &ws->bar[s], pol_stream);
     bulk_g2s(ws->xt[s], a.X + r0 * a.k, xbytes, &ws->bar[s], pol_keep);
 }
 
-template <int K>
-__global__ void __launch_bounds__(SpmmCfg<K>::WARPS * 32, SpmmCfg<K>::MINB) k_spmm_sym_tiled(SpmmArgs a) {
-    using C = SpmmCfg<K>;
-    constexpr int RPL = C::RPL, GK = C::GK, S = C::STAGES;
+__device__ __forceinline__ int4 load_rec(const ChunkRec *p, int64_t c) {
+    return __ldg(reinterpret_cast<const int4 *>(p + c));
+}
+
+template <int NT>
+__global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_spmm_sym_tiled(SpmmArgs a) {
+    using C = SpmmCfg<NT>;
+    constexpr int S = C::STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * C::WARPS + warp;
     if (gw >= a.W) return;
-    WarpSmem<K> *ws = reinterpret_cast<WarpSmem<K> *>(smem_raw) + warp;
+    WarpSmem<NT> *ws = reinterpret_cast<WarpSmem<NT> *>(smem_raw) + warp;
     const int rb0 = a.warp_rb[gw], rb1 = a.warp_rb[gw + 1];
     if (rb0 >= rb1) return;
     const int64_t c0 = a.rb_chunk[rb0], c1 = a.rb_chunk[rb1];
-    const int kg = lane % GK, rg = lane / GK;
-    const bool kact = kg * 4 < a.k;
+    const int g = lane >> 2, t = lane & 3;   // mma fragment coordinates
     const int k = a.k;
 
     if (lane == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&ws->bar[s], 1);
+        for (int st = 0; st < S; ++st) mbar_init(&ws->bar[st], 1);
         fence_proxy_async();
     }
     __syncwarp();
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
-    if (lane == 0)
-        for (int s = 0; s < S; ++s)
-            if (c0 + s < c1) issue_chunk<K>(a, ws, c0 + s, s, pol_stream, pol_keep);
+    // lane 0 issues; the record of the chunk after next is loaded one step early
+    int4 pending = make_int4(0, 0, 0, 0);
+    if (lane == 0) {
+        for (int st = 0; st < S; ++st)
+            if (c0 + st < c1) issue_chunk<NT>(a, ws, load_rec(a.chunk, c0 + st), st, pol_stream, pol_keep);
+        if (c0 + S < c1) pending = load_rec(a.chunk, c0 + S);
+    }
 
-    float xr[TILE][4];
-    float yr[RPL][4];
+    float yr[NT][4];      // Y_R accumulators (D fragments)
+    uint32_t xbh[2][NT][2], xbl[2][NT][2];   // X_R as split B fragments [k-step][n-tile][b0,b1]
 #pragma unroll
-    for (int j = 0; j < RPL; ++j)
+    for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yr[j][q] = 0.f;
-#pragma unroll
-    for (int r = 0; r < TILE; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) xr[r][q] = 0.f;
+        for (int q = 0; q < 4; ++q) yr[nt][q] = 0.f;
     int64_t cur_rb = -1;
+    int cur_rows = 0;
     uint32_t phases = 0;
+    int s = 0, yb = 0;
 
-    auto flush_yr = [&](int64_t rb) {
-        if (!kact) return;
+    // Add a 16 x k tile from registers (D-fragment layout) to Y rows r0.. via
+    // shared memory and one bulk reduce.
+    auto reduce_tile = [&](const float (&d)[NT][4], int64_t r0, int rows) {
+        if (lane == 0) bulk_wait_read<1>();   // buffer yb was read by the reduce two tiles ago
+        __syncwarp();
+        float *yt = ws->yt[yb];
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            const int64_t row = rb * TILE + rg * RPL + j;
-            if (row < a.n) red_add_v4(a.Y + row * k + kg * 4, yr[j][0], yr[j][1], yr[j][2], yr[j][3]);
+        for (int nt = 0; nt < NT; ++nt) {
+            const int col = 8 * nt + 2 * t;
+            if (col < k) {
+                *reinterpret_cast<float2 *>(yt + g * k + col) = make_float2(d[nt][0], d[nt][1]);
+                *reinterpret_cast<float2 *>(yt + (g + 8) * k + col) = make_float2(d[nt][2], d[nt][3]);
+            }
         }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_reduce_add_f32(a.Y + r0 * k, yt, static_cast<uint32_t>(rows * k) * 4u);
+            bulk_commit();
+        }
+        yb ^= 1;
     };
 
     for (int64_t c = c0; c < c1; ++c) {
-        const int s = static_cast<int>((c - c0) % S);
         const bool ok = mbar_wait_bounded(&ws->bar[s], (phases >> s) & 1u);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(a.err, DEV_TIMEOUT);
             // let copies already in flight land before the warp leaves
+            int ss = s;
             for (int64_t cc = c; cc < c1 && cc < c + S; ++cc) {
-                const int ss = static_cast<int>((cc - c0) % S);
                 mbar_wait_bounded(&ws->bar[ss], (phases >> ss) & 1u);
+                ss = (ss + 1 == S) ? 0 : ss + 1;
             }
+            if (lane == 0) bulk_wait<0>();
             return;
         }
         phases ^= 1u << s;
@@ -145,104 +214,111 @@ __global__ void __launch_bounds__(SpmmCfg<K>::WARPS * 32, SpmmCfg<K>::MINB) k_sp
         const int ct = m.x, cnt = m.y & 0xFFFF, rows = m.w;
         const bool is_diag = (m.y & DIAG_FLAG) != 0;
         const float *xt = ws->xt[s];
+        const uint32_t *sidx = ws->cd[s];
+        const float *sval = reinterpret_cast<const float *>(ws->cd[s] + m.z);
 
-        if (is_diag) {
-            if (cur_rb >= 0) flush_yr(cur_rb);
-            cur_rb = ct;
-#pragma unroll
-            for (int j = 0; j < RPL; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) yr[j][q] = 0.f;
-#pragma unroll
-            for (int r = 0; r < TILE; ++r) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (kact && r < rows) v = *reinterpret_cast<const float4 *>(xt + r * k + kg * 4);
-                xr[r][0] = v.x; xr[r][1] = v.y; xr[r][2] = v.z; xr[r][3] = v.w;
-            }
-            // symmetric tile S = L + L^T - D of the diagonal block, in HT
-            for (int e = lane; e < TILE * 18; e += 32) ws->HT[e] = 0.f;
-            __syncwarp();
-            for (int e = lane; e < cnt; e += 32) {
-                const uint32_t u = ws->idx[s][e];
-                const float v = ws->vals[s][e];
-                const int rl = (u >> 28) & 15, cl = u & 15;
-                ws->HT[rl * 18 + cl] = v;
-                ws->HT[cl * 18 + rl] = v;
+        // scatter: zero the tiles unless every position will be written (a
+        // full 256-entry tile, or a diagonal chunk holding all 136 entries of
+        // its lower triangle), then place the entries, four per lane per step
+        if (cnt < (is_diag ? 136 : 256)) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = lane; e < TILE * HS / 4; e += 32) {
+                reinterpret_cast<float4 *>(ws->H)[e] = z;
+                reinterpret_cast<float4 *>(ws->HT)[e] = z;
             }
             __syncwarp();
+        }
+        for (int e = lane * 4; e < cnt; e += 128) {
+            const uint4 u4 = *reinterpret_cast<const uint4 *>(sidx + e);
+            const float4 v4 = *reinterpret_cast<const float4 *>(sval + e);
+            const uint32_t uu[4] = {u4.x, u4.y, u4.z, u4.w};
+            const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-            for (int cc = 0; cc < TILE; ++cc) {
-                float sv[RPL];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) sv[j] = ws->HT[cc * 18 + rg * RPL + j];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) yr[j][q] = fmaf(sv[j], xr[cc][q], yr[j][q]);
-            }
-        } else {
-            const bool full = (cnt == 256);
-            const float *Hp = full ? ws->vals[s] : ws->H;
-            if (!full) {
-                for (int e = lane; e < 256; e += 32) ws->H[e] = 0.f;
-                for (int e = lane; e < TILE * 18; e += 32) ws->HT[e] = 0.f;
-                __syncwarp();
-            }
-            for (int e = lane; e < cnt; e += 32) {
-                const uint32_t u = ws->idx[s][e];
-                const float v = ws->vals[s][e];
-                const int rl = (u >> 28) & 15, cl = u & 15;
-                ws->HT[cl * 18 + rl] = v;
-                if (!full) ws->H[rl * 16 + cl] = v;
-            }
-            __syncwarp();
-            // Y_R += H_t X_C
-#pragma unroll
-            for (int cc = 0; cc < TILE; ++cc) {
-                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (kact) x = *reinterpret_cast<const float4 *>(xt + cc * k + kg * 4);
-                float hv[RPL];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) hv[j] = ws->HT[cc * 18 + rg * RPL + j];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    yr[j][0] = fmaf(hv[j], x.x, yr[j][0]);
-                    yr[j][1] = fmaf(hv[j], x.y, yr[j][1]);
-                    yr[j][2] = fmaf(hv[j], x.z, yr[j][2]);
-                    yr[j][3] = fmaf(hv[j], x.w, yr[j][3]);
-                }
-            }
-            // Y_C = H_t^T X_R
-            float yc[RPL][4];
-#pragma unroll
-            for (int j = 0; j < RPL; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) yc[j][q] = 0.f;
-#pragma unroll
-            for (int r = 0; r < TILE; ++r) {
-                float hv[RPL];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) hv[j] = Hp[r * 16 + rg * RPL + j];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) yc[j][q] = fmaf(hv[j], xr[r][q], yc[j][q]);
-            }
-            if (kact) {
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    const int64_t row = static_cast<int64_t>(ct) * TILE + rg * RPL + j;
-                    red_add_v4(a.Y + row * k + kg * 4, yc[j][0], yc[j][1], yc[j][2], yc[j][3]);
+            for (int q = 0; q < 4; ++q) {
+                if (e + q < cnt) {
+                    const int rl = (uu[q] >> 28) & 15, cl = uu[q] & 15;
+                    ws->H[rl * HS + cl] = vv[q];
+                    if (is_diag) ws->H[cl * HS + rl] = vv[q];   // S = L + L^T - D
+                    else ws->HT[cl * HS + rl] = vv[q];
                 }
             }
         }
         __syncwarp();
-        if (lane == 0 && c + S < c1) {
-            fence_proxy_async();
-            issue_chunk<K>(a, ws, c + S, s, pol_stream, pol_keep);
+
+        if (is_diag) {
+            if (cur_rb >= 0) reduce_tile(yr, cur_rb * TILE, cur_rows);
+            cur_rb = ct;
+            cur_rows = rows;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yr[nt][q] = 0.f;
+            // X_R B fragments: b0 = X_R[8ks+t][8nt+g], b1 = X_R[8ks+t+4][8nt+g]
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int col = 8 * nt + g, r0 = 8 * ks + t;
+                    const float v0 = (col < k && r0 < rows) ? xt[r0 * k + col] : 0.f;
+                    const float v1 = (col < k && r0 + 4 < rows) ? xt[(r0 + 4) * k + col] : 0.f;
+                    split_tf32(v0, xbh[ks][nt][0], xbl[ks][nt][0]);
+                    split_tf32(v1, xbh[ks][nt][1], xbl[ks][nt][1]);
+                }
+            // Y_R += S X_R
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t ah[4], al[4];
+                load_a(ws->H, ks, g, t, ah, al);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+                    mma3(yr[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
+            }
+        } else {
+            // Each tile product starts from a zero accumulator and is added to
+            // Y_R with ordinary FP32 adds: the tensor-core accumulation then
+            // only ever sums the 48 terms of one tile product.
+            float yc[NT][4], yt4[NT][4];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yc[nt][q] = yt4[nt][q] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t ah[4], al[4];
+                // Y_R += H_t X_C
+                load_a(ws->H, ks, g, t, ah, al);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int col = 8 * nt + g, r0 = 8 * ks + t;
+                    uint32_t bh0, bl0, bh1, bl1;
+                    split_tf32(col < k ? xt[r0 * k + col] : 0.f, bh0, bl0);
+                    split_tf32(col < k ? xt[(r0 + 4) * k + col] : 0.f, bh1, bl1);
+                    mma3(yt4[nt], ah, al, bh0, bh1, bl0, bl1);
+                }
+                // Y_C = H_t^T X_R
+                load_a(ws->HT, ks, g, t, ah, al);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+                    mma3(yc[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yr[nt][q] += yt4[nt][q];
+            reduce_tile(yc, static_cast<int64_t>(ct) * TILE, TILE);   // off-diagonal tiles lie inside 0..n-1
         }
+        __syncwarp();
+        if (c + S < c1) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_chunk<NT>(a, ws, pending, s, pol_stream, pol_keep);
+                if (c + S + 1 < c1) pending = load_rec(a.chunk, c + S + 1);
+            }
+        }
+        s = (s + 1 == S) ? 0 : s + 1;
     }
-    if (cur_rb >= 0) flush_yr(cur_rb);
+    if (cur_rb >= 0) reduce_tile(yr, cur_rb * TILE, cur_rows);
+    if (lane == 0) bulk_wait<0>();   // reduces complete before the warp's shared memory goes away
 }
 
 // ---------------------------------------------------------------------------
@@ -259,9 +335,8 @@ struct SimpleSmem {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const uint32_t *idx, const float *val,
-                                                         const int64_t *chunk_off, const int32_t *chunk_ct,
-                                                         const int32_t *chunk_info, const int64_t *rb_chunk,
+__global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const uint32_t *data,
+                                                         const ChunkRec *chunk, const int64_t *rb_chunk,
                                                          int64_t R, const T *X, T *Y) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -279,17 +354,21 @@ __global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const
         for (int t = 0; t < 16; ++t) acc[t] = T(0);
         __syncwarp();
         for (int64_t c = rb_chunk[rb]; c < rb_chunk[rb + 1]; ++c) {
-            const int64_t off = chunk_off[c];
-            const int info = chunk_info[c];
+            const ChunkRec rec = chunk[c];
+            const int64_t off = rec.off;
+            const int info = rec.info;
+            const int64_t npad = (info >> NPAD_SHIFT) & 0x3FF;
+            const uint32_t *cidx = data + 2 * off;
+            const uint32_t *cval = cidx + npad;
             const int cnt = info & 0xFFFF;
             const bool is_diag = (info & DIAG_FLAG) != 0;
-            const int64_t ct = chunk_ct[c];
+            const int64_t ct = rec.ct;
             for (int e = lane; e < 256; e += 32) ws->H[e] = 0.f;
             for (int e = lane; e < TILE * 17; e += 32) ws->HT[e] = 0.f;
             __syncwarp();
             for (int e = lane; e < cnt; e += 32) {
-                const uint32_t u = idx[off + e];
-                const float v = val[off + e];
+                const uint32_t u = cidx[e];
+                const float v = __uint_as_float(cval[e]);
                 const int rl = (u >> 28) & 15, cl = u & 15;
                 ws->H[rl * 16 + cl] = v;
                 if (is_diag) ws->H[cl * 16 + rl] = v;
@@ -333,24 +412,23 @@ __global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const
 
 // ---------------------------------------------------------------------------
 
-template <int K>
+template <int NT>
 static cudaError_t launch_tiled(const lobpcg_ctx *h, const float *X, float *Y, int k, cudaStream_t s) {
-    using C = SpmmCfg<K>;
-    const size_t smem = sizeof(WarpSmem<K>) * C::WARPS;
+    using C = SpmmCfg<NT>;
+    const size_t smem = sizeof(WarpSmem<NT>) * C::WARPS;
     static bool attr_set[64] = {false};
     int dev = h->device;
     if (!attr_set[dev & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(k_spmm_sym_tiled<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_spmm_sym_tiled<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         attr_set[dev & 63] = true;
     }
     SpmmArgs a;
-    a.n = h->T.n; a.k = k; a.idx = h->T.idx; a.val = h->T.val; a.chunk_off = h->T.chunk_off;
-    a.chunk_ct = h->T.chunk_ct; a.chunk_info = h->T.chunk_info; a.rb_chunk = h->T.rb_chunk;
+    a.n = h->T.n; a.k = k; a.data = h->T.data; a.chunk = h->T.chunk; a.rb_chunk = h->T.rb_chunk;
     a.warp_rb = h->T.warp_rb; a.W = h->T.warps; a.X = X; a.Y = Y; a.err = h->d_err;
     const int blocks = (h->T.warps + C::WARPS - 1) / C::WARPS;
-    k_spmm_sym_tiled<K><<<blocks, C::WARPS * 32, smem, s>>>(a);
+    k_spmm_sym_tiled<NT><<<blocks, C::WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -368,8 +446,7 @@ static cudaError_t launch_simple(const lobpcg_ctx *h, const T *X, T *Y, int k, c
     const int64_t R = h->T.R;
     int blocks = static_cast<int>(std::min<int64_t>((R + 7) / 8, static_cast<int64_t>(h->num_sms) * 8));
     if (blocks < 1) blocks = 1;
-    k_spmm_sym_simple<T><<<blocks, 256, smem, s>>>(h->T.n, k, h->T.idx, h->T.val, h->T.chunk_off, h->T.chunk_ct,
-                                                   h->T.chunk_info, h->T.rb_chunk, R, X, Y);
+    k_spmm_sym_simple<T><<<blocks, 256, smem, s>>>(h->T.n, k, h->T.data, h->T.chunk, h->T.rb_chunk, R, X, Y);
     return cudaGetLastError();
 }
 
@@ -378,9 +455,10 @@ cudaError_t launch_spmm_sym_f32(const lobpcg_ctx *h, const float *X, float *Y, i
     if (e != cudaSuccess) return e;
     const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
     if (aligned && k % 4 == 0) {
-        if (k <= 8) return launch_tiled<8>(h, X, Y, k, s);
-        if (k <= 16) return launch_tiled<16>(h, X, Y, k, s);
-        return launch_tiled<32>(h, X, Y, k, s);
+        if (k <= 8) return launch_tiled<1>(h, X, Y, k, s);
+        if (k <= 16) return launch_tiled<2>(h, X, Y, k, s);
+        if (k <= 24) return launch_tiled<3>(h, X, Y, k, s);
+        return launch_tiled<4>(h, X, Y, k, s);
     }
     return launch_simple<float>(h, X, Y, k, s);
 }

@@ -46,8 +46,7 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *row_ptr, const
 template <bool FILL, typename VT>
 __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const int32_t *col, const VT *val,
                             int64_t *cnt_chunks, int64_t *cnt_npad, int64_t *cnt_full, const int64_t *rb_chunk,
-                            const int64_t *rb_nnz, uint32_t *idx, float *oval, int64_t *chunk_off,
-                            int32_t *chunk_ct, int32_t *chunk_info) {
+                            const int64_t *rb_nnz, uint32_t *data, ChunkRec *chunk) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t rb = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); rb < R;
@@ -66,13 +65,19 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
         if (FILL) {
             base = rb_nnz[rb];
             cidx = rb_chunk[rb];
-            const int64_t o = base + warp_excl_scan_i32(dcnt);
+            // words [2 base, 2 base + dpad): indices; [2 base + dpad, 2 base + 2 dpad): values
+            uint32_t *ci = data + 2 * base, *cv = ci + dpad;
+            const int o = warp_excl_scan_i32(dcnt);
             for (int t = 0; t < dcnt; ++t) {
-                idx[o + t] = static_cast<uint32_t>(col[q + t]) | (static_cast<uint32_t>(lane) << 28);
-                oval[o + t] = static_cast<float>(val[q + t]);
+                ci[o + t] = static_cast<uint32_t>(col[q + t]) | (static_cast<uint32_t>(lane) << 28);
+                cv[o + t] = __float_as_uint(static_cast<float>(val[q + t]));
             }
-            if (lane < dpad - dtot) { idx[base + dtot + lane] = IDX_PAD; oval[base + dtot + lane] = 0.f; }
-            if (lane == 0) { chunk_off[cidx] = base; chunk_ct[cidx] = static_cast<int32_t>(rb); chunk_info[cidx] = dtot | DIAG_FLAG; }
+            if (lane < dpad - dtot) { ci[dtot + lane] = IDX_PAD; cv[dtot + lane] = 0u; }
+            if (lane == 0) {
+                ChunkRec r;
+                r.off = base; r.ct = static_cast<int32_t>(rb); r.info = dtot | DIAG_FLAG | (dpad << NPAD_SHIFT);
+                chunk[cidx] = r;
+            }
             base += dpad;
             ++cidx;
         }
@@ -86,13 +91,18 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
             const int tot = warp_sum_i32(c_l);
             const int tpad = (tot + 3) & ~3;
             if (FILL) {
-                const int64_t o = base + warp_excl_scan_i32(c_l);
+                uint32_t *ci = data + 2 * base, *cv = ci + tpad;
+                const int o = warp_excl_scan_i32(c_l);
                 for (int t = 0; t < c_l; ++t) {
-                    idx[o + t] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
-                    oval[o + t] = static_cast<float>(val[p + t]);
+                    ci[o + t] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
+                    cv[o + t] = __float_as_uint(static_cast<float>(val[p + t]));
                 }
-                if (lane < tpad - tot) { idx[base + tot + lane] = IDX_PAD; oval[base + tot + lane] = 0.f; }
-                if (lane == 0) { chunk_off[cidx] = base; chunk_ct[cidx] = m; chunk_info[cidx] = tot; }
+                if (lane < tpad - tot) { ci[tot + lane] = IDX_PAD; cv[tot + lane] = 0u; }
+                if (lane == 0) {
+                    ChunkRec r;
+                    r.off = base; r.ct = m; r.info = tot | (tpad << NPAD_SHIFT);
+                    chunk[cidx] = r;
+                }
                 base += tpad;
                 ++cidx;
             } else {
@@ -187,8 +197,7 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     const int wpb = 8;
     const int64_t tblocks = std::min<int64_t>((R + wpb - 1) / wpb, 65535LL * 16);
     k_tile_rows<false, VT><<<static_cast<unsigned>(tblocks), wpb * 32, 0, s>>>(
-        n, R, row_ptr, col, val, d_cnt, d_cnt + R, d_cnt + 2 * R, nullptr, nullptr, nullptr, nullptr, nullptr,
-        nullptr, nullptr);
+        n, R, row_ptr, col, val, d_cnt, d_cnt + R, d_cnt + 2 * R, nullptr, nullptr, nullptr, nullptr);
     TRY(cudaGetLastError());
     std::vector<int64_t> cnt(3 * R);
     TRY(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * 3 * R, cudaMemcpyDeviceToHost, s));
@@ -206,21 +215,16 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     T.full_chunks = full;
 
     // 3. allocate the tiled arrays and fill them
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.idx), sizeof(uint32_t) * std::max<int64_t>(T.npad, 4)));
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.val), sizeof(float) * std::max<int64_t>(T.npad, 4)));
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk_off), sizeof(int64_t) * (T.nchunks + 1)));
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk_ct), sizeof(int32_t) * T.nchunks));
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk_info), sizeof(int32_t) * T.nchunks));
+    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.data), sizeof(uint32_t) * 2 * std::max<int64_t>(T.npad, 4)));
+    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk), sizeof(ChunkRec) * T.nchunks));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.rb_chunk), sizeof(int64_t) * (R + 1)));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.diag), sizeof(float) * n));
     int64_t *d_rb_nnz = nullptr;
     TRY(cudaMallocAsync(&d_rb_nnz, sizeof(int64_t) * (R + 1), s));
     TRY(cudaMemcpyAsync(T.rb_chunk, rb_chunk.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
     TRY(cudaMemcpyAsync(d_rb_nnz, rb_nnz.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(T.chunk_off + T.nchunks, &rb_nnz[R], sizeof(int64_t), cudaMemcpyHostToDevice, s));
     k_tile_rows<true, VT><<<static_cast<unsigned>(tblocks), wpb * 32, 0, s>>>(
-        n, R, row_ptr, col, val, nullptr, nullptr, nullptr, T.rb_chunk, d_rb_nnz, T.idx, T.val, T.chunk_off,
-        T.chunk_ct, T.chunk_info);
+        n, R, row_ptr, col, val, nullptr, nullptr, nullptr, T.rb_chunk, d_rb_nnz, T.data, T.chunk);
     TRY(cudaGetLastError());
     k_diag<VT><<<static_cast<unsigned>(gblocks), tpb, 0, s>>>(n, row_ptr, col, val, T.diag);
     TRY(cudaGetLastError());
@@ -240,7 +244,10 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
 
     // 5. partition row blocks over the SpMM warps, balancing padded entries
     //    plus a per-chunk and per-row-block overhead
-    const int64_t want = static_cast<int64_t>(h->num_sms) * 16;
+#ifndef SPMM_WARPS_PER_SM
+#define SPMM_WARPS_PER_SM 16
+#endif
+    const int64_t want = static_cast<int64_t>(h->num_sms) * SPMM_WARPS_PER_SM;
     const int W = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, R)));
     std::vector<int32_t> warp_rb(W + 1);
     auto cost = [&](int64_t r) { return rb_nnz[r] + 32 * rb_chunk[r] + 64 * r; };
