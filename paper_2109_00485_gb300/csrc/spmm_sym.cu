@@ -39,7 +39,7 @@ namespace lobpcg {
 #define SPMM_MINB 2
 #endif
 
-constexpr int HS = 20;   // row stride of the scattered tiles: fragment loads are bank-conflict free
+constexpr int HS = 20;   // row stride of the scattered tile (fragment loads of T: bank-conflict free)
 
 // NT = number of 8-column n-tiles of the vector block (k <= 8 NT).
 template <int NT>
@@ -55,8 +55,7 @@ struct __align__(16) WarpSmem {
     uint32_t cd[SpmmCfg<NT>::STAGES][512];        // one chunk: npad index words, then npad value words
     float xt[SpmmCfg<NT>::STAGES][TILE * 8 * NT];  // X rows of the chunk's column tile (row stride k)
     float yt[2][TILE * 8 * NT];                     // Y tiles handed to the bulk reduce (double-buffered)
-    float H[TILE * HS];                             // tile (or symmetric diagonal tile), row-major
-    float HT[TILE * HS];                            // transposed tile
+    float H[TILE * HS];                             // scattered tile (or symmetric diagonal tile), row-major
     int4 meta[SpmmCfg<NT>::STAGES];                 // column tile, info, padded count, valid rows
     uint64_t bar[SpmmCfg<NT>::STAGES];
 };
@@ -86,7 +85,7 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) 
 
 // d += a b  (m16n8k8, TF32 inputs, FP32 accumulate)
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -101,14 +100,25 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], con
     mma_tf32(d, ah, bh0, bh1);
 }
 
-// A fragment (16x8 slice ks of a 16x16 tile stored row-major with stride HS):
+// A fragment (16x8 slice ks) of a 16x16 tile T stored with row stride RS:
 // a0 = T[g][8ks+t], a1 = T[g+8][8ks+t], a2 = T[g][8ks+t+4], a3 = T[g+8][8ks+t+4].
+template <int RS>
 __device__ __forceinline__ void load_a(const float *T, int ks, int g, int t, uint32_t (&ah)[4], uint32_t (&al)[4]) {
-    const float *p = T + g * HS + 8 * ks + t;
+    const float *p = T + g * RS + 8 * ks + t;
     split_tf32(p[0], ah[0], al[0]);
-    split_tf32(p[8 * HS], ah[1], al[1]);
+    split_tf32(p[8 * RS], ah[1], al[1]);
     split_tf32(p[4], ah[2], al[2]);
-    split_tf32(p[8 * HS + 4], ah[3], al[3]);
+    split_tf32(p[8 * RS + 4], ah[3], al[3]);
+}
+// The same fragment of the TRANSPOSE of T (T stored with row stride RS):
+// a0 = T[8ks+t][g], a1 = T[8ks+t][g+8], a2 = T[8ks+t+4][g], a3 = T[8ks+t+4][g+8].
+template <int RS>
+__device__ __forceinline__ void load_at(const float *T, int ks, int g, int t, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+    const float *p = T + (8 * ks + t) * RS + g;
+    split_tf32(p[0], ah[0], al[0]);
+    split_tf32(p[8], ah[1], al[1]);
+    split_tf32(p[4 * RS], ah[2], al[2]);
+    split_tf32(p[4 * RS + 8], ah[3], al[3]);
 }
 
 // Issue the bulk copies of one chunk into stage s (one lane).
@@ -217,33 +227,25 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         const uint32_t *sidx = ws->cd[s];
         const float *sval = reinterpret_cast<const float *>(ws->cd[s] + m.z);
 
-        // scatter: zero the tiles unless every position will be written (a
-        // full 256-entry tile, or a diagonal chunk holding all 136 entries of
-        // its lower triangle), then place the entries, four per lane per step
-        if (cnt < (is_diag ? 136 : 256)) {
+        // A chunk holding all 256 entries of its off-diagonal tile is that tile
+        // in row-major order (indices unique and sorted), so its fragments
+        // are read straight from the staged values.  Any other chunk is
+        // scattered by its indices into a zeroed tile (the diagonal chunk
+        // into the symmetric S = L + L^T - D).
+        const bool full = !is_diag && cnt == 256;
+        if (!full) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int e = lane; e < TILE * HS / 4; e += 32) {
-                reinterpret_cast<float4 *>(ws->H)[e] = z;
-                reinterpret_cast<float4 *>(ws->HT)[e] = z;
+            for (int e = lane; e < TILE * HS / 4; e += 32) reinterpret_cast<float4 *>(ws->H)[e] = z;
+            __syncwarp();
+            for (int e = lane; e < cnt; e += 32) {
+                const uint32_t u = sidx[e];
+                const float v = sval[e];
+                const int rl = (u >> 28) & 15, cl = u & 15;
+                ws->H[rl * HS + cl] = v;
+                if (is_diag) ws->H[cl * HS + rl] = v;
             }
             __syncwarp();
         }
-        for (int e = lane * 4; e < cnt; e += 128) {
-            const uint4 u4 = *reinterpret_cast<const uint4 *>(sidx + e);
-            const float4 v4 = *reinterpret_cast<const float4 *>(sval + e);
-            const uint32_t uu[4] = {u4.x, u4.y, u4.z, u4.w};
-            const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (e + q < cnt) {
-                    const int rl = (uu[q] >> 28) & 15, cl = uu[q] & 15;
-                    ws->H[rl * HS + cl] = vv[q];
-                    if (is_diag) ws->H[cl * HS + rl] = vv[q];   // S = L + L^T - D
-                    else ws->HT[cl * HS + rl] = vv[q];
-                }
-            }
-        }
-        __syncwarp();
 
         if (is_diag) {
             if (cur_rb >= 0) reduce_tile(yr, cur_rb * TILE, cur_rows);
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t ah[4], al[4];
-                load_a(ws->H, ks, g, t, ah, al);
+                load_a<HS>(ws->H, ks, g, t, ah, al);
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
                     mma3(yr[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
@@ -284,22 +286,37 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
                 for (int q = 0; q < 4; ++q) yc[nt][q] = yt4[nt][q] = 0.f;
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-                uint32_t ah[4], al[4];
-                // Y_R += H_t X_C
-                load_a(ws->H, ks, g, t, ah, al);
+                uint32_t ah[4], al[4], th[4], tl[4];
+                if (full) {
+                    load_a<16>(sval, ks, g, t, ah, al);    // H_t
+                    load_at<16>(sval, ks, g, t, th, tl);   // H_t^T
+                } else {
+                    load_a<HS>(ws->H, ks, g, t, ah, al);
+                    load_at<HS>(ws->H, ks, g, t, th, tl);
+                }
+                uint32_t bh[NT][2], bl[NT][2];
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt) {
                     const int col = 8 * nt + g, r0 = 8 * ks + t;
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split_tf32(col < k ? xt[r0 * k + col] : 0.f, bh0, bl0);
-                    split_tf32(col < k ? xt[(r0 + 4) * k + col] : 0.f, bh1, bl1);
-                    mma3(yt4[nt], ah, al, bh0, bh1, bl0, bl1);
+                    split_tf32(col < k ? xt[r0 * k + col] : 0.f, bh[nt][0], bl[nt][0]);
+                    split_tf32(col < k ? xt[(r0 + 4) * k + col] : 0.f, bh[nt][1], bl[nt][1]);
                 }
-                // Y_C = H_t^T X_R
-                load_a(ws->HT, ks, g, t, ah, al);
+                // small terms first, independent accumulators interleaved
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-                    mma3(yc[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
+                for (int nt = 0; nt < NT; ++nt) {
+                    mma_tf32(yt4[nt], al, bh[nt][0], bh[nt][1]);                          // Y_R += H_t X_C
+                    mma_tf32(yc[nt], tl, xbh[ks][nt][0], xbh[ks][nt][1]);                 // Y_C = H_t^T X_R
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    mma_tf32(yt4[nt], ah, bl[nt][0], bl[nt][1]);
+                    mma_tf32(yc[nt], th, xbl[ks][nt][0], xbl[ks][nt][1]);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    mma_tf32(yt4[nt], ah, bh[nt][0], bh[nt][1]);
+                    mma_tf32(yc[nt], th, xbh[ks][nt][0], xbh[ks][nt][1]);
+                }
             }
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt)
