@@ -84,6 +84,19 @@ typedef struct {
     uint64_t seed;
 } lobpcg_params;
 
+/* Counters of one lobpcg_solve. */
+typedef struct {
+    int32_t iters;             /* LOBPCG iterations (one SpMM H W each), both phases */
+    int32_t iters_fp64;        /* of which in the float64 refinement phase */
+    int32_t used_fp64;         /* 1 if the float64 phase ran */
+    int32_t converged;         /* 1 if all nev residuals met tol (explicit re-check) */
+    int32_t p_dropped;         /* Rayleigh-Ritz steps that dropped P (O not positive definite) */
+    int32_t svqb_used;         /* orthonormalisations that fell back to SVQB */
+    int32_t explicit_restarts; /* convergence claims refuted by the explicit SpMM re-check */
+    int32_t reserved;
+    double time_ms;            /* wall time of the solve */
+} lobpcg_stats;
+
 /* Facts about the stored matrix and its device layout (lobpcg_matrix_info). */
 typedef struct {
     int64_t n, nnz;          /* as given */
@@ -153,6 +166,57 @@ LOBPCG_API lobpcg_status lobpcg_spmm_sym(lobpcg_t h, const float *X, float *Y, i
  * and polish converged eigenpairs.  k: 1..32.
  */
 LOBPCG_API lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double *Y, int32_t k);
+
+/*
+ * W = K^{-1} R: the preconditioning step of Algorithm 1 (line 6), K the
+ * block-diagonal matrix of shifted diagonal tiles of H (Section 3.3).  The
+ * shift for column j is theta[j]; a shifted pivot t is guarded as
+ * g(t) = sign(t) max(|t|, 1e-3 max(1, |theta_j|)).
+ *   mode 0: K = I (W = R)
+ *   mode 1: 1x1 tiles, w_ij = r_ij / g(h_ii - theta_j)
+ *   mode 2: 64-row tiles solved exactly through their eigendecompositions
+ *           (needs params.precond == 2 at create, else ERR_UNSUPPORTED)
+ *   mode 3: the learned tile network (after lobpcg_precond_train)
+ *   R, W  : float32 n x k row-major, device (may be the same buffer)
+ *   theta : float64[k], device
+ */
+LOBPCG_API lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *theta, float *W,
+                                              int32_t k, int32_t mode);
+
+/*
+ * Rayleigh-Ritz on the subspace spanned by the m columns of S (eq. rreig):
+ * G = S^T (H S), O = S^T S (FP64 accumulation), then the k leftmost
+ * eigenpairs of the pencil G C = O C D.  Cholesky of O first; if O is not
+ * numerically positive definite, the eigendecomposition of O with
+ * directions below 1e-12 of its largest eigenvalue dropped.
+ *   S, HS : float32 n x m row-major, device (HS = H S, e.g. from spmm_sym)
+ *   m     : 1..96;  k: 1..m
+ *   C     : float64 m x k row-major, device;  theta: float64[k], device
+ * Returns ERR_BREAKDOWN if fewer than k directions remain.
+ */
+LOBPCG_API lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, int32_t m, int32_t k,
+                                              double *C, double *theta);
+
+/*
+ * The k leftmost eigenpairs of H by block LOBPCG (Algorithm 1), with the
+ * preconditioner, tolerance and limits of the create parameters.  Only one
+ * SpMM (H W) per iteration: HX and HP follow the recurrences of eqs.
+ * upd1-upd2.  The iteration runs with float32 vectors; when its residual
+ * stalls above tol (float32 rounding) and params.polish_fp64 is set, it
+ * continues with float64 vectors.  Convergence is confirmed with an explicit
+ * SpMM.
+ *   X     : float32 n x k row-major; in: initial guess X0, out: Ritz vectors
+ *           (device or host pointer; host memory is copied in and out)
+ *   evals : host float64[nev], Ritz values ascending
+ *   resid : host float64[nev], relative residual norms (params.resid_mode)
+ *   st    : host stats (may be NULL)
+ * Returns OK, ERR_NOT_CONVERGED (outputs still written), ERR_BREAKDOWN,
+ * ERR_NONFINITE, ERR_CUDA.  Synchronises the stream.
+ */
+LOBPCG_API lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, lobpcg_stats *st);
+
+/* The last solve's Ritz vectors in float64 (n x k row-major, device or host). */
+LOBPCG_API lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X);
 
 #ifdef __cplusplus
 }

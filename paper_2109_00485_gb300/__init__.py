@@ -44,6 +44,12 @@ class _Params(ctypes.Structure):
                 ("polish_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
+class _Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("iters_fp64", ctypes.c_int32), ("used_fp64", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("p_dropped", ctypes.c_int32), ("svqb_used", ctypes.c_int32),
+                ("explicit_restarts", ctypes.c_int32), ("reserved", ctypes.c_int32), ("time_ms", ctypes.c_double)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_blocks", ctypes.c_int64),
                 ("chunks", ctypes.c_int64), ("padded_nnz", ctypes.c_int64), ("full_chunks", ctypes.c_int64),
@@ -79,6 +85,14 @@ def load():
     L.lobpcg_spmm_sym.restype = st
     L.lobpcg_spmm_sym_f64.argtypes = [vp, vp, vp, i32]
     L.lobpcg_spmm_sym_f64.restype = st
+    L.lobpcg_precond_apply.argtypes = [vp, vp, vp, vp, i32, i32]
+    L.lobpcg_precond_apply.restype = st
+    L.lobpcg_rayleigh_ritz.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    L.lobpcg_rayleigh_ritz.restype = st
+    L.lobpcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Stats)]
+    L.lobpcg_solve.restype = st
+    L.lobpcg_get_x_f64.argtypes = [vp, vp]
+    L.lobpcg_get_x_f64.restype = st
     _lib = L
     return L
 
@@ -149,6 +163,65 @@ class Handle:
         _check(self._h, load().lobpcg_spmm_sym_f64(self._h, _ptr(X), _ptr(Y), k))
         return Y
 
+    def lobpcg_precond_apply(self, R, theta, W=None, mode="diag"):
+        """W = K^{-1} R (float32 device n x k); theta: float64 device tensor (k)."""
+        import torch
+        k = R.shape[1]
+        _dev_block(R, "f32", self.n, k)
+        if W is None:
+            W = torch.empty_like(R)
+        _dev_block(W, "f32", self.n, k)
+        if not (theta.is_cuda and theta.dtype == torch.float64 and theta.numel() == k and theta.is_contiguous()):
+            raise ValueError("theta must be a contiguous CUDA float64 tensor of length k")
+        m = PRECOND[mode] if isinstance(mode, str) else int(mode)
+        _check(self._h, load().lobpcg_precond_apply(self._h, _ptr(R), _ptr(theta), _ptr(W), k, m))
+        return W
+
+    def lobpcg_rayleigh_ritz(self, S, HS, k: int):
+        """(C, theta) of the k leftmost Ritz pairs in span(S): S, HS float32
+        device n x m; returns float64 device tensors C (m x k), theta (k)."""
+        import torch
+        m = S.shape[1]
+        _dev_block(S, "f32", self.n, m)
+        _dev_block(HS, "f32", self.n, m)
+        C = torch.empty((m, k), dtype=torch.float64, device=S.device)
+        th = torch.empty((k,), dtype=torch.float64, device=S.device)
+        _check(self._h, load().lobpcg_rayleigh_ritz(self._h, _ptr(S), _ptr(HS), m, k, _ptr(C), _ptr(th)))
+        return C, th
+
+    def lobpcg_solve(self, X0):
+        """Run LOBPCG from X0 (float32 n x k: CUDA tensor, or host numpy / CPU
+        tensor).  Returns (X, evals, resid, stats) with X of the same kind;
+        raises LobpcgError on failure (NOT_CONVERGED carries .result)."""
+        k = self.params.k
+        nev = self.params.nev
+        if isinstance(X0, np.ndarray):
+            X = np.ascontiguousarray(X0, dtype=np.float32).copy()
+            if X.shape != (self.n, k):
+                raise ValueError(f"X0 must be ({self.n}, {k})")
+        else:
+            X = X0.detach().clone().contiguous()
+            if tuple(X.shape) != (self.n, k) or str(X.dtype) != "torch.float32":
+                raise ValueError(f"X0 must be float32 ({self.n}, {k})")
+        ev = np.zeros(nev)
+        rs = np.zeros(nev)
+        stats = _Stats()
+        status = load().lobpcg_solve(self._h, _ptr(X), ev.ctypes.data, rs.ctypes.data, ctypes.byref(stats))
+        result = (X, ev, rs, {f: getattr(stats, f) for f, _ in _Stats._fields_})
+        if status != LOBPCG_OK:
+            err = LobpcgError(status, self.lobpcg_last_error())
+            err.result = result
+            raise err
+        return result
+
+    def lobpcg_get_x_f64(self, out=None):
+        import torch
+        k = self.params.k
+        if out is None:
+            out = torch.empty((self.n, k), dtype=torch.float64, device="cuda")
+        _check(self._h, load().lobpcg_get_x_f64(self._h, _ptr(out)))
+        return out
+
     def lobpcg_sync(self):
         _check(self._h, load().lobpcg_sync(self._h))
 
@@ -169,6 +242,10 @@ class Handle:
     # -- conveniences with the same meaning ---------------------------------
     spmm_sym = lobpcg_spmm_sym
     spmm_sym_f64 = lobpcg_spmm_sym_f64
+    precond_apply = lobpcg_precond_apply
+    rayleigh_ritz = lobpcg_rayleigh_ritz
+    solve = lobpcg_solve
+    get_x_f64 = lobpcg_get_x_f64
     sync = lobpcg_sync
     info = lobpcg_matrix_info
     destroy = lobpcg_destroy

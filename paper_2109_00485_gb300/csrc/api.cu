@@ -6,8 +6,10 @@
 #include <string>
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "dense.h"
 #include "internal.h"
 #include "lobpcg.h"
+#include "precond.h"
 
 using namespace lobpcg;
 
@@ -28,6 +30,7 @@ void release(lobpcg_ctx *h) {
     if (!h) return;
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    solver_release(h);
     if (h->stage_x) cudaFree(h->stage_x);
     if (h->stage_y) cudaFree(h->stage_y);
     h->stage_x = h->stage_y = nullptr;
@@ -128,6 +131,9 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     std::string err;
     lobpcg_status st = LOBPCG_ERR_CUDA;
     e = build_tiled(h, rp, cl, vl, A->val_is_fp64 != 0, err, st);
+    if (e == cudaSuccess && st == LOBPCG_OK && P.precond == 2) e = bjacobi_setup(h, rp, cl, vl, A->val_is_fp64 != 0);
+    if (e == cudaSuccess && st == LOBPCG_OK) e = solver_setup(h);
+    if (e == cudaSuccess && st == LOBPCG_OK) e = cudaStreamSynchronize(h->stream);
     if (tmp) {
         cudaFreeAsync(tmp, h->stream);
         cudaStreamSynchronize(h->stream);
@@ -220,6 +226,62 @@ lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double *Y, int32_
     if (ranges_overlap(X, bytes, Y, bytes)) return fail(h, LOBPCG_ERR_ARG, "X and Y overlap");
     cudaError_t e = launch_spmm_sym_f64(h, X, Y, k, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "spmm_sym_f64");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *theta, float *W, int32_t k,
+                                   int32_t mode) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!R || !W || !theta) return fail(h, LOBPCG_ERR_ARG, "R, W or theta is NULL");
+    if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
+    if (mode < 0 || mode > 3) return fail(h, LOBPCG_ERR_ARG, "mode must be 0..3");
+    if (mode == 2 && !h->bj_Q) return fail(h, LOBPCG_ERR_UNSUPPORTED, "block-Jacobi needs params.precond = 2 at create");
+    if (mode == 3) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner not trained");
+    cudaError_t e = precond_apply<float>(h, mode, k, R, theta, W, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "precond_apply");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, int32_t m, int32_t k, double *C,
+                                   double *theta) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!S || !HS || !C || !theta) return fail(h, LOBPCG_ERR_ARG, "S, HS, C or theta is NULL");
+    if (m < 1 || m > 96 || k < 1 || k > m) return fail(h, LOBPCG_ERR_ARG, "need 1 <= k <= m <= 96");
+    double *G = nullptr, *O = nullptr;
+    int *status = nullptr;
+    cudaError_t e = cudaMallocAsync(&G, sizeof(double) * (2 * m * m + 1), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rayleigh_ritz");
+    O = G + m * m;
+    status = reinterpret_cast<int *>(O + m * m);
+    GemmBlocks<float> a{}, b{};
+    a.p[0] = S;
+    b.p[0] = HS;
+    e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream);
+    if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream);
+    if (e == cudaSuccess) e = launch_rayleigh_ritz(m, k, m, G, O, nullptr, C, theta, status, h->stream);
+    int hs = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFreeAsync(G, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rayleigh_ritz");
+    if (hs == 2) return fail(h, LOBPCG_ERR_BREAKDOWN, "fewer than k directions in span(S)");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, lobpcg_stats *st) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!X) return fail(h, LOBPCG_ERR_ARG, "X is NULL");
+    if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
+    std::string err;
+    lobpcg_status s = solve(h, X, is_host_ptr(X), evals, resid, st, err);
+    if (s != LOBPCG_OK) return fail(h, s, err);
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X) {
+    if (!h || !X) return LOBPCG_ERR_ARG;
+    cudaError_t e = copy_x_f64(h, X);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_x_f64");
     return LOBPCG_OK;
 }
 

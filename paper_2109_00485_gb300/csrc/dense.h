@@ -1,0 +1,39 @@
+// Launchers for the dense LOBPCG steps (dense.cu) and the preconditioners.
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lobpcg {
+
+// Up to six n x k blocks addressed as one n x (nb k) matrix [B_0 .. B_5].
+template <typename T>
+struct GemmBlocks {
+    const T *p[6];
+};
+
+// Up to two outputs of k_combine: z[o] = A[:, c0[o]:] C[o]; C[o] is
+// (na k - c0[o]) x k FP64 row-major.  norm_of: output whose squared column
+// norms are accumulated (or -1).
+template <typename T>
+struct CombineOut {
+    T *z[2];
+    const double *C[2];
+    int c0[2];
+    int norm_of;
+};
+
+template <typename T>
+cudaError_t launch_resid(int64_t n, int k, const T *X, const T *HX, const double *theta, const float *d, T *W,
+                         int mode, double *norms, int num_sms, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmBlocks<T> b, double *M, int num_sms,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
+                           int num_sms, cudaStream_t s);
+cudaError_t launch_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, const double *pscale,
+                                 double *C, double *theta, int *status, cudaStream_t s);
+cudaError_t launch_orth_factor(int k, const double *B, double *T, int *status, cudaStream_t s);
+
+}  // namespace lobpcg

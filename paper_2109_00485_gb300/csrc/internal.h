@@ -8,6 +8,8 @@
 
 namespace lobpcg {
 
+struct SolverState;
+
 // One 16-byte record per chunk (see Tiled).
 struct __align__(16) ChunkRec {
     int64_t off;
@@ -60,6 +62,9 @@ struct lobpcg_ctx {
     float *stage_x = nullptr;    // device staging of host X / Y blocks (spmm_sym with host pointers)
     float *stage_y = nullptr;
     size_t stage_k = 0;
+    float *bj_Q = nullptr;       // block-Jacobi: per 64-row tile eigenvectors (64 x 64) and eigenvalues
+    float *bj_lam = nullptr;
+    lobpcg::SolverState *solver = nullptr;  // workspaces of lobpcg_solve (solver.cu)
     std::string last_error;
 };
 
@@ -75,5 +80,12 @@ cudaError_t launch_spmm_sym_f64(const lobpcg_ctx *h, const double *X, double *Y,
 
 // helpers in api.cu
 cudaError_t dev_alloc(lobpcg_ctx *h, void **p, size_t bytes);
+
+// solver.cu
+cudaError_t solver_setup(lobpcg_ctx *h);
+void solver_release(lobpcg_ctx *h);
+lobpcg_status solve(lobpcg_ctx *h, float *X, bool x_on_host, double *evals, double *resid, lobpcg_stats *st,
+                    std::string &err);
+cudaError_t copy_x_f64(lobpcg_ctx *h, double *out);
 
 }  // namespace lobpcg

@@ -1,0 +1,388 @@
+// lobpcg_solve: block LOBPCG (Algorithm 1) driven from the host, every step
+// on the device, one stream, one small device->host read per iteration (the
+// residual norms for the convergence test).
+//
+// Per iteration (in the paper's order):
+//   R = HX - X Theta, column norms; W = K^{-1} R               (lines 6, 10-11)
+//   W <- W - X (X^T W); Cholesky-QR (SVQB on breakdown); twice  (Section 3.4)
+//   HW = H W  (the one SpMM per iteration)                      (eqs. upd1-upd2)
+//   G = S^T HS, O = S^T S for S = [X W P], HS = [HX HW HP]      (eq. go)
+//   Rayleigh-Ritz on (G, O), P columns scaled to unit norm      (eq. rreig)
+//   X = S C, HX = HS C, P = [W P] C_23, HP = [HW HP] C_23       (eqs. xupd, pupd, upd1, upd2)
+// The iteration runs with float32 vectors and SpMM; when the float32
+// residual stops improving above the tolerance (its rounding floor), the
+// solve continues from the current X with float64 vectors, the float64
+// SpMM and the same steps.  On exit HX is recomputed by an explicit SpMM and
+// the test repeated.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "dense.h"
+#include "internal.h"
+#include "lobpcg.h"
+#include "precond.h"
+
+namespace lobpcg {
+
+template <typename T>
+struct Blocks {
+    T *X = nullptr, *HX = nullptr, *W = nullptr, *HW = nullptr, *P = nullptr, *HP = nullptr;
+};
+
+struct SolverState {
+    int k = 0;
+    Blocks<float> f;
+    Blocks<double> d;
+    double *G = nullptr, *O = nullptr, *C = nullptr, *theta = nullptr, *norms = nullptr, *colsqP = nullptr;
+    double *pscale = nullptr, *B = nullptr, *Tm = nullptr, *Cproj = nullptr;
+    int *status = nullptr;       // [0] RR status, [1] orthonormalisation status
+    double *h_buf = nullptr;     // pinned: norms (2k), theta (k), status (2 as doubles)
+};
+
+__global__ void k_proj_coef(int k, const double *B, double *Cp) {
+    // Cp = [I; -B]  (2k x k): W - X B = [W X] Cp
+    for (int e = threadIdx.x; e < 2 * k * k; e += blockDim.x) {
+        const int r = e / k, j = e % k;
+        Cp[e] = (r < k) ? (r == j ? 1.0 : 0.0) : -B[(r - k) * k + j];
+    }
+}
+
+__global__ void k_pscale(int k, const double *colsq, double *ps) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ps[j] = colsq[j] > 0.0 ? 1.0 / sqrt(colsq[j]) : 1.0;
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int64_t m, const A *in, B *out) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[e] = static_cast<B>(in[e]);
+}
+
+}  // namespace lobpcg
+
+using namespace lobpcg;
+
+namespace {
+
+#define CK(x)                                        \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return e_;            \
+    } while (0)
+
+template <typename T>
+cudaError_t spmm_T(lobpcg_ctx *h, const T *X, T *Y, int k);
+template <>
+cudaError_t spmm_T<float>(lobpcg_ctx *h, const float *X, float *Y, int k) {
+    return launch_spmm_sym_f32(h, X, Y, k, h->stream);
+}
+template <>
+cudaError_t spmm_T<double>(lobpcg_ctx *h, const double *X, double *Y, int k) {
+    return launch_spmm_sym_f64(h, X, Y, k, h->stream);
+}
+
+template <typename T>
+Blocks<T> &blocks_of(SolverState *s);
+template <>
+Blocks<float> &blocks_of<float>(SolverState *s) { return s->f; }
+template <>
+Blocks<double> &blocks_of<double>(SolverState *s) { return s->d; }
+
+struct PhaseResult {
+    int iters = 0;
+    bool converged = false;
+    bool stagnated = false;
+    std::vector<double> rho;
+    std::vector<double> theta;
+};
+
+// Read norms + theta + statuses (one sync); compute rho on the host.
+template <typename T>
+cudaError_t read_progress(lobpcg_ctx *h, SolverState *s, std::vector<double> &rho, std::vector<double> &theta,
+                          int *rr_status, int *orth_status) {
+    const int k = s->k;
+    CK(cudaMemcpyAsync(s->h_buf, s->norms, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(s->h_buf + 2 * k, s->theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(reinterpret_cast<int *>(s->h_buf + 3 * k), s->status, sizeof(int) * 2, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    rho.resize(k);
+    theta.resize(k);
+    const double G = h->gershgorin;
+    for (int j = 0; j < k; ++j) {
+        const double rn = std::sqrt(std::max(0.0, s->h_buf[j])), xn = std::sqrt(std::max(0.0, s->h_buf[k + j]));
+        const double th = s->h_buf[2 * k + j];
+        theta[j] = th;
+        const double den = (h->params.resid_mode == 0) ? std::max(std::fabs(th), 1e-12 * G) * xn : G * xn;
+        rho[j] = den > 0 ? rn / den : INFINITY;
+    }
+    const int *st = reinterpret_cast<const int *>(s->h_buf + 3 * k);
+    *rr_status = st[0];
+    *orth_status = st[1];
+    return cudaSuccess;
+}
+
+// One orthonormalisation pass: W <- W - X (X^T W), then W <- W T with the
+// Cholesky-QR (or SVQB) factor T of W^T W.
+template <typename T>
+cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    GemmBlocks<T> ax{}, aw{};
+    ax.p[0] = b.X;
+    aw.p[0] = b.W;
+    CK(launch_gram<T>(n, k, 1, ax, 1, aw, s->B, h->num_sms, h->stream));          // B = X^T W
+    k_proj_coef<<<1, 256, 0, h->stream>>>(k, s->B, s->Cproj);
+    CK(cudaGetLastError());
+    GemmBlocks<T> awx{};
+    awx.p[0] = b.W;
+    awx.p[1] = b.X;
+    CombineOut<T> o1{};
+    o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1;
+    CK(launch_combine<T>(n, k, 2, awx, 1, o1, nullptr, h->num_sms, h->stream));   // W -= X B
+    CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream));          // B = W^T W
+    CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
+    CombineOut<T> o2{};
+    o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1;
+    return launch_combine<T>(n, k, 1, aw, 1, o2, nullptr, h->num_sms, h->stream);  // W <- W T
+}
+
+// Rayleigh-Ritz on X alone (Algorithm 1, lines 1-2): X <- X C, HX <- HX C.
+template <typename T>
+cudaError_t rr_on_x(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    GemmBlocks<T> ax{}, ahx{};
+    ax.p[0] = b.X;
+    ahx.p[0] = b.HX;
+    CK(launch_gram<T>(n, k, 1, ax, 1, ahx, s->G, h->num_sms, h->stream));
+    CK(launch_gram<T>(n, k, 1, ax, 1, ax, s->O, h->num_sms, h->stream));
+    CK(launch_rayleigh_ritz(k, k, k, s->G, s->O, nullptr, s->C, s->theta, s->status, h->stream));
+    CombineOut<T> ox{}, oh{};
+    ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0; ox.norm_of = -1;
+    oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0; oh.norm_of = -1;
+    CK(launch_combine<T>(n, k, 1, ax, 1, ox, nullptr, h->num_sms, h->stream));
+    return launch_combine<T>(n, k, 1, ahx, 1, oh, nullptr, h->num_sms, h->stream);
+}
+
+template <typename T>
+cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on_stagnation, PhaseResult &res,
+                      lobpcg_stats *st, lobpcg_status &status) {
+    const int k = s->k, nev = h->params.nev;
+    const int64_t n = h->T.n;
+    const double tol = h->params.tol;
+    Blocks<T> &b = blocks_of<T>(s);
+    const int pmode = h->params.precond;
+    status = LOBPCG_OK;
+
+    CK(spmm_T<T>(h, b.X, b.HX, k));
+    CK(rr_on_x<T>(h, s, b));
+    bool hasP = false;
+    double best = INFINITY;
+    int since_best = 0;
+    int restarts = 0;
+    std::vector<double> rho, theta;
+    while (true) {
+        // R = HX - X Theta and norms; W = K^{-1} R
+        CK(launch_resid<T>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
+                           h->stream));
+        int rr_st = 0, orth_st = 0;
+        CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st));
+        if (rr_st == 2) {
+            status = LOBPCG_ERR_BREAKDOWN;
+            break;
+        }
+        if (rr_st == 1 && st) st->p_dropped++;
+        if (orth_st == 1 && st) st->svqb_used++;
+        bool finite = true;
+        for (int j = 0; j < k; ++j) finite = finite && std::isfinite(rho[j]) && std::isfinite(theta[j]);
+        if (!finite) {
+            status = LOBPCG_ERR_NONFINITE;
+            break;
+        }
+        double worst = 0.0;
+        for (int j = 0; j < nev; ++j) worst = std::max(worst, rho[j]);
+        if (worst <= tol) {
+            // explicit re-check: HX from a fresh SpMM (into HW as scratch)
+            CK(spmm_T<T>(h, b.X, b.HW, k));
+            CK(launch_resid<T>(n, k, b.X, b.HW, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms,
+                               h->num_sms, h->stream));
+            CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st));
+            double worst_e = 0.0;
+            for (int j = 0; j < nev; ++j) worst_e = std::max(worst_e, rho[j]);
+            if (worst_e <= tol || restarts >= 5) {
+                res.converged = worst_e <= tol;
+                break;
+            }
+            ++restarts;
+            if (st) st->explicit_restarts++;
+            CK(cudaMemcpyAsync(b.HX, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
+            continue;
+        }
+        if (worst < 0.7 * best) {
+            best = worst;
+            since_best = 0;
+        } else if (++since_best >= 15 && stop_on_stagnation) {
+            res.stagnated = true;
+            break;
+        }
+        if (res.iters >= max_iters) break;
+        ++res.iters;
+        // preconditioner (the diagonal one was applied inside the residual kernel)
+        if (pmode == 2) CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
+        // orthonormalise W against X and itself
+        CK(orth_pass<T>(h, s, b));
+        CK(orth_pass<T>(h, s, b));
+        // the one SpMM per iteration
+        CK(spmm_T<T>(h, b.W, b.HW, k));
+        // Gram matrices of S = [X W P], HS = [HX HW HP]
+        const int na = hasP ? 3 : 2;
+        const int m = na * k;
+        GemmBlocks<T> aS{}, aHS{};
+        aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
+        aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
+        CK(launch_gram<T>(n, k, na, aS, na, aHS, s->G, h->num_sms, h->stream));
+        CK(launch_gram<T>(n, k, na, aS, na, aS, s->O, h->num_sms, h->stream));
+        if (hasP) {
+            k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
+            CK(cudaGetLastError());
+        }
+        CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->O, hasP ? s->pscale : nullptr, s->C, s->theta, s->status,
+                                h->stream));
+        // X = S C, P = [W P] C_23 (with ||p_j||^2), HX = HS C, HP = [HW HP] C_23
+        CombineOut<T> ox{}, oh{};
+        ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0;
+        ox.z[1] = b.P; ox.C[1] = s->C + static_cast<int64_t>(k) * k; ox.c0[1] = k; ox.norm_of = 1;
+        oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0;
+        oh.z[1] = b.HP; oh.C[1] = s->C + static_cast<int64_t>(k) * k; oh.c0[1] = k; oh.norm_of = -1;
+        CK(launch_combine<T>(n, k, na, aS, 2, ox, s->colsqP, h->num_sms, h->stream));
+        CK(launch_combine<T>(n, k, na, aHS, 2, oh, nullptr, h->num_sms, h->stream));
+        hasP = true;
+    }
+    res.rho = rho;
+    res.theta = theta;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t alloc_blocks(lobpcg_ctx *h, Blocks<T> &b, int k) {
+    const size_t bytes = sizeof(T) * static_cast<size_t>(h->T.n) * k;
+    for (T **p : {&b.X, &b.HX, &b.W, &b.HW, &b.P, &b.HP}) CK(dev_alloc(h, reinterpret_cast<void **>(p), bytes));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace lobpcg {
+
+cudaError_t solver_setup(lobpcg_ctx *h) {
+    const int k = h->params.k;
+    SolverState *s = new SolverState();
+    h->solver = s;
+    s->k = k;
+    CK(alloc_blocks<float>(h, s->f, k));
+    if (h->params.polish_fp64) CK(alloc_blocks<double>(h, s->d, k));
+    const int m = 3 * k;
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->G), sizeof(double) * m * m));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->O), sizeof(double) * m * m));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->C), sizeof(double) * m * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->theta), sizeof(double) * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->norms), sizeof(double) * 2 * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->colsqP), sizeof(double) * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->pscale), sizeof(double) * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->B), sizeof(double) * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->Tm), sizeof(double) * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cproj), sizeof(double) * 2 * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->status), sizeof(int) * 4));
+    CK(cudaMemsetAsync(s->status, 0, sizeof(int) * 4, h->stream));
+    CK(cudaMallocHost(reinterpret_cast<void **>(&s->h_buf), sizeof(double) * (4 * k + 4)));
+    return cudaSuccess;
+}
+
+void solver_release(lobpcg_ctx *h) {
+    if (!h->solver) return;
+    if (h->solver->h_buf) cudaFreeHost(h->solver->h_buf);
+    delete h->solver;
+    h->solver = nullptr;
+}
+
+// The full solve (see the file comment).  X: n x k float32 (device or host),
+// in: initial guess, out: Ritz vectors.
+lobpcg_status solve(lobpcg_ctx *h, float *Xio, bool x_on_host, double *evals, double *resid, lobpcg_stats *st,
+                    std::string &err) {
+    SolverState *s = h->solver;
+    const int k = s->k, nev = h->params.nev;
+    const int64_t n = h->T.n;
+    const size_t bytes32 = sizeof(float) * n * k;
+    auto t0 = std::chrono::steady_clock::now();
+    if (st) std::memset(st, 0, sizeof(*st));
+    cudaError_t e = cudaMemcpyAsync(s->f.X, Xio, bytes32, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) { err = std::string("solve: ") + cudaGetErrorString(e); return LOBPCG_ERR_CUDA; }
+    PhaseResult r32;
+    lobpcg_status status = LOBPCG_OK;
+    e = run_phase<float>(h, s, h->params.maxiter, h->params.polish_fp64 != 0, r32, st, status);
+    if (e != cudaSuccess) { err = std::string("solve (fp32): ") + cudaGetErrorString(e); return LOBPCG_ERR_CUDA; }
+    PhaseResult final = r32;
+    int iters64 = 0;
+    bool used64 = false;
+    if (status == LOBPCG_OK && !r32.converged && h->params.polish_fp64 && s->d.X) {
+        // continue in float64 from the current X
+        const int64_t m = n * k;
+        k_convert<float, double><<<std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((m + 255) / 256))), 256, 0,
+                                   h->stream>>>(m, s->f.X, s->d.X);
+        PhaseResult r64;
+        e = run_phase<double>(h, s, std::max(0, h->params.maxiter - r32.iters), false, r64, st, status);
+        if (e != cudaSuccess) { err = std::string("solve (fp64): ") + cudaGetErrorString(e); return LOBPCG_ERR_CUDA; }
+        iters64 = r64.iters;
+        final = r64;
+        used64 = true;
+        const int64_t mm = n * k;
+        k_convert<double, float><<<std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((mm + 255) / 256))), 256,
+                                   0, h->stream>>>(mm, s->d.X, s->f.X);
+    }
+    if (!used64 && s->d.X) {   // keep a float64 copy for lobpcg_get_x_f64
+        const int64_t mm = n * k;
+        k_convert<float, double><<<std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((mm + 255) / 256))), 256,
+                                   0, h->stream>>>(mm, s->f.X, s->d.X);
+    }
+    e = cudaMemcpyAsync(Xio, s->f.X, bytes32, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { err = std::string("solve: ") + cudaGetErrorString(e); return LOBPCG_ERR_CUDA; }
+    for (int j = 0; j < nev && j < static_cast<int>(final.theta.size()); ++j) {
+        if (evals) evals[j] = final.theta[j];
+        if (resid) resid[j] = final.rho[j];
+    }
+    if (st) {
+        st->iters = r32.iters + iters64;
+        st->iters_fp64 = iters64;
+        st->used_fp64 = used64 ? 1 : 0;
+        st->converged = final.converged ? 1 : 0;
+        st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != LOBPCG_OK) {
+        err = status == LOBPCG_ERR_BREAKDOWN ? "Rayleigh-Ritz breakdown" : "non-finite residual";
+        return status;
+    }
+    if (!final.converged) {
+        err = "maxiter reached before the residual tolerance";
+        return LOBPCG_ERR_NOT_CONVERGED;
+    }
+    return LOBPCG_OK;
+}
+
+cudaError_t copy_x_f64(lobpcg_ctx *h, double *out) {
+    SolverState *s = h->solver;
+    if (!s || !s->d.X) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(out, s->d.X, sizeof(double) * h->T.n * s->k, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e;
+}
+
+}  // namespace lobpcg
