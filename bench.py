@@ -1,12 +1,17 @@
 #!/usr/bin/env python3
-"""Benchmark: symmetric SpMM GB/s on the n = 2M workload (one GB300).
+"""Benchmark: symmetric SpMM GB/s inside LOBPCG on the n = 2M workload (one GB300).
 
-One step = one symmetric SpMM Y = H X over the whole stored triangle (n = 2M,
-~400 stored entries per row, k = 16, float32), inputs resident in HBM.  The
-matrix stream (~6.4 GB) is far larger than L2, so no explicit flush is done.
+One step = one LOBPCG iteration on the n = 2M matrix (~400 stored entries per
+row, k = 16, nev = 8, float32, diagonal preconditioner): residual and
+preconditioner, two Cholesky-QR passes, the SpMM H W, Gram matrices,
+Rayleigh-Ritz and the update -- every row of the hot path -- with inputs
+resident in HBM.  The matrix stream (~6.4 GB) is far larger than L2, so no
+explicit flush is done.
 
-value      : algorithmic SpMM bytes per step x steps / timed region (GB/s),
+value      : SpMM algorithmic bytes per step x steps / timed region (GB/s),
              algorithmic bytes = nnz (4 col + 4 val) + 8 (n + 1) + 2 n k 4.
+lobpcg     : time-to-solution (nev pairs at relative residual 1e-6) of
+             lobpcg_solve from a host X0, per preconditioner.
 e2e        : the same metric through lobpcg_spmm_sym with pinned HOST X and Y
              (host->device copy of X and device->host copy of Y each step).
 roofline   : the spmm_sym kernel alone, timed with CUDA events on its stream,
@@ -182,14 +187,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi")):
+    """Time-to-solution (relative residual 1e-6, nev pairs) from a host X0,
+    through lobpcg_solve; create (matrix tiling, preconditioner set-up) is
+    timed separately."""
+    import torch
+    out = {}
+    X0 = synth.initial_guess(A, p["k"], seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
+    for pc in precs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc, polish_fp64=1,
+                         stream=stream)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        try:
+            X, ev, rs, st = h.solve(X0)
+            ok = True
+        except pkg.LobpcgError as e:
+            X, ev, rs, st = e.result
+            ok = False
+        t_solve = time.perf_counter() - t0
+        h.destroy()
+        out[pc] = {"time_to_solution_s": round(t_solve, 3), "create_s": round(t_create, 3),
+                   "iters": st["iters"], "iters_fp64": st["iters_fp64"], "converged": bool(ok and st["converged"]),
+                   "max_resid": float(np.max(rs)), "evals": [float(v) for v in ev]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -207,16 +242,16 @@ def main():
     pkg.load()
 
     p = synth.WORKLOADS[args.workload]
-    pinned = lambda shape, dt: torch.empty(shape, dtype={np.int64: torch.int64, np.int32: torch.int32,
-                                                         np.float32: torch.float32, np.float64: torch.float64}[dt],
-                                           pin_memory=True).numpy()
+    tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32, np.float64: torch.float64}
+    pinned = lambda shape, dt: torch.empty(shape, dtype=tdt[dt], pin_memory=True).numpy()
     A = synth.tile_matrix(p["n"], p["nnz_per_row"], seed=p["seed"], fp32=True, alloc=pinned)
     n, k, nnz = A.n, p["k"], A.nnz
     stream = torch.cuda.Stream(device=dev)
+    h = pkg.from_csr(A, k=k, nev=p["nev"], tol=1e-6, maxiter=1000, precond="diag", stream=stream)
+    X0 = synth.initial_guess(A, k, seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
     with torch.cuda.stream(stream):
-        h = pkg.from_csr(A, k=k, nev=p["nev"], stream=stream)
-        X = torch.from_numpy(synth.normal_block(n, k, seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)).to(dev)
-        Y = torch.empty_like(X)
+        X0d = torch.from_numpy(X0).to(dev)
+    torch.cuda.synchronize()
     info = h.info()
     B = alg_bytes(n, nnz, k)
 
@@ -225,32 +260,22 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    # warm-up
-    for _ in range(max(args.warmup, 3)):
-        h.spmm_sym(X, Y)
-    h.sync()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # warm-up: start a run from X0 and take W iterations
+    h.iterate(max(args.warmup, 3), X0=X0d)
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    t_all0 = torch.cuda.Event(enable_timing=True)
-    t_all1 = torch.cuda.Event(enable_timing=True)
-    t_all0.record(stream)
-    for i in range(args.steps):
-        starts[i].record(stream)
-        h.spmm_sym(X, Y)
-        ends[i].record(stream)
-    t_all1.record(stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    theta, st = h.iterate(args.steps)          # the timed steps: K LOBPCG iterations
+    e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    h.sync()
-    total_ms = t_all0.elapsed_time(t_all1)
-    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = e0.elapsed_time(e1)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev)
@@ -258,10 +283,11 @@ def main():
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
     value = B * args.steps * world / (total_ms / 1e3) / 1e9
+    spmm_ms = st["spmm_ms"] / max(1, st["spmm_calls"])
 
-    # e2e through the C ABI with pinned host buffers
+    # e2e: the same metric through lobpcg_spmm_sym with pinned HOST X and Y
     Xh = torch.empty((n, k), dtype=torch.float32, pin_memory=True)
-    Xh.copy_(X.cpu())
+    Xh.copy_(torch.from_numpy(X0))
     Yh = torch.empty((n, k), dtype=torch.float32, pin_memory=True)
     h.spmm_sym_host(Xh, Yh)
     h.sync()
@@ -273,16 +299,21 @@ def main():
     h.sync()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": round(B * world / e2e_s / 1e9, 2), "unit": "GB/s",
-           "h2d_bytes_per_step": n * k * 4, "d2h_bytes_per_step": n * k * 4}
+           "h2d_bytes_per_step": n * k * 4, "d2h_bytes_per_step": n * k * 4,
+           "call": "lobpcg_spmm_sym with pinned host X, Y"}
+    h.destroy()
 
     peaks = measured_peaks()
-    spmm_ms = statistics.mean(per)
     achieved = B / (spmm_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": recorded_traffic(args.workload),
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "kernel": "k_spmm_sym_tiled<16>", "alg_bytes_per_launch": B}
+                "kernel": "k_spmm_sym_tiled<2> (k=16)", "alg_bytes_per_launch": B,
+                "kernel_ms": round(spmm_ms, 4)}
 
+    solves = None
+    if rank == 0 and not args.no_solves:
+        solves = lobpcg_solves(pkg, A, p, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A, k)
@@ -292,18 +323,19 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "n": n, "nnz": nnz, "k": k,
+                "config": {"workload": args.workload, "n": n, "nnz": nnz, "k": k, "nev": p["nev"],
+                           "step": "one LOBPCG iteration (residual+diag preconditioner, 2x CholQR, SpMM H W, "
+                                   "Gram, Rayleigh-Ritz, update); value = SpMM algorithmic bytes per step / step time",
                            "structure": "16x16 dense tiles, 90% within 5% of the diagonal, 10% scattered",
                            "l2": "inputs (6.4 GB matrix stream) larger than L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps,
-                "gflops": round(4.0 * k * nnz / (spmm_ms / 1e3) / 1e9, 1),
-                "spmm_ms_median": round(statistics.median(per), 4),
+                "gpu_launches": 20 * args.steps,
+                "gflops_spmm": round(4.0 * k * nnz / (spmm_ms / 1e3) / 1e9, 1),
+                "lobpcg": solves,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],
                            "padded_nnz": info["padded_nnz"], "warps": info["warps"]}}
         print(json.dumps(line), flush=True)
-    h.destroy()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

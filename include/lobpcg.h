@@ -93,8 +93,9 @@ typedef struct {
     int32_t p_dropped;         /* Rayleigh-Ritz steps that dropped P (O not positive definite) */
     int32_t svqb_used;         /* orthonormalisations that fell back to SVQB */
     int32_t explicit_restarts; /* convergence claims refuted by the explicit SpMM re-check */
-    int32_t reserved;
-    double time_ms;            /* wall time of the solve */
+    int32_t spmm_calls;        /* H W products timed below */
+    double time_ms;            /* wall time of the call */
+    double spmm_ms;            /* device time of the H W products (CUDA events on the handle's stream) */
 } lobpcg_stats;
 
 /* Facts about the stored matrix and its device layout (lobpcg_matrix_info). */
@@ -214,6 +215,17 @@ LOBPCG_API lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const 
  * ERR_NONFINITE, ERR_CUDA.  Synchronises the stream.
  */
 LOBPCG_API lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, lobpcg_stats *st);
+
+/*
+ * Run exactly `steps` float32 LOBPCG iterations (Algorithm 1, lines 6-12,
+ * without the exit test; the residual norms are still formed and read back
+ * each iteration as in lobpcg_solve).  X0 (n x k float32, device or host)
+ * starts a new run from X0; X0 == NULL continues the previous run on this
+ * handle.  theta (host float64[k], may be NULL) receives the current Ritz
+ * values.  For benchmarking one iteration of the method.
+ */
+LOBPCG_API lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double *theta,
+                                        lobpcg_stats *st);
 
 /* The last solve's Ritz vectors in float64 (n x k row-major, device or host). */
 LOBPCG_API lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X);

@@ -30,7 +30,8 @@ Readings where the paper is silent (each listed in the design notes):
     2002) which drops directions with sigma < 1e-12 sigma_max;
   * P and HP columns are scaled to unit ||p_j|| before the Rayleigh-Ritz step;
   * if O is not numerically positive definite (Cholesky fails or its
-    pivots span more than 1e7), P is dropped for that iteration;
+    pivots span more than 1e4, i.e. cond(O) above about 1e8), P is dropped
+    for that iteration;
   * on exit HX is recomputed by an explicit SpMM and convergence re-checked;
     if it no longer holds the iteration continues from the explicit HX.
 """
@@ -65,7 +66,7 @@ def tri_inv_lower(L: np.ndarray) -> np.ndarray:
     return Inv
 
 
-def rayleigh_ritz(G: np.ndarray, O: np.ndarray, k: int, pivot_span: float = 1e7):
+def rayleigh_ritz(G: np.ndarray, O: np.ndarray, k: int, pivot_span: float = 1e4):
     """Solve the pencil G C = O C D (eq. rreig) and keep the k leftmost pairs.
 
     O = L L^T (Cholesky); G_hat = L^{-1} G L^{-T}; G_hat = V D V^T (Jacobi);

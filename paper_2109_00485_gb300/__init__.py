@@ -47,7 +47,8 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("iters_fp64", ctypes.c_int32), ("used_fp64", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("p_dropped", ctypes.c_int32), ("svqb_used", ctypes.c_int32),
-                ("explicit_restarts", ctypes.c_int32), ("reserved", ctypes.c_int32), ("time_ms", ctypes.c_double)]
+                ("explicit_restarts", ctypes.c_int32), ("spmm_calls", ctypes.c_int32), ("time_ms", ctypes.c_double),
+                ("spmm_ms", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -91,6 +92,8 @@ def load():
     L.lobpcg_rayleigh_ritz.restype = st
     L.lobpcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Stats)]
     L.lobpcg_solve.restype = st
+    L.lobpcg_iterate.argtypes = [vp, vp, i32, vp, ctypes.POINTER(_Stats)]
+    L.lobpcg_iterate.restype = st
     L.lobpcg_get_x_f64.argtypes = [vp, vp]
     L.lobpcg_get_x_f64.restype = st
     _lib = L
@@ -214,6 +217,15 @@ class Handle:
             raise err
         return result
 
+    def lobpcg_iterate(self, steps: int, X0=None):
+        """Run `steps` float32 iterations (X0 starts a new run; None
+        continues).  Returns (theta, stats)."""
+        th = np.zeros(self.params.k)
+        stats = _Stats()
+        _check(self._h, load().lobpcg_iterate(self._h, _ptr(X0) if X0 is not None else None, int(steps),
+                                              th.ctypes.data, ctypes.byref(stats)))
+        return th, {f: getattr(stats, f) for f, _ in _Stats._fields_}
+
     def lobpcg_get_x_f64(self, out=None):
         import torch
         k = self.params.k
@@ -245,6 +257,7 @@ class Handle:
     precond_apply = lobpcg_precond_apply
     rayleigh_ritz = lobpcg_rayleigh_ritz
     solve = lobpcg_solve
+    iterate = lobpcg_iterate
     get_x_f64 = lobpcg_get_x_f64
     sync = lobpcg_sync
     info = lobpcg_matrix_info

@@ -258,7 +258,7 @@ lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, 
     b.p[0] = HS;
     e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream);
     if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream);
-    if (e == cudaSuccess) e = launch_rayleigh_ritz(m, k, m, G, O, nullptr, C, theta, status, h->stream);
+    if (e == cudaSuccess) e = launch_rayleigh_ritz(m, k, m, G, O, m, nullptr, C, theta, status, h->stream);
     int hs = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -274,6 +274,16 @@ lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, l
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
     std::string err;
     lobpcg_status s = solve(h, X, is_host_ptr(X), evals, resid, st, err);
+    if (s != LOBPCG_OK) return fail(h, s, err);
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double *theta, lobpcg_stats *st) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (steps < 0) return fail(h, LOBPCG_ERR_ARG, "steps must be >= 0");
+    if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
+    std::string err;
+    lobpcg_status s = iterate(h, X0, X0 ? is_host_ptr(X0) : false, steps, theta, st, err);
     if (s != LOBPCG_OK) return fail(h, s, err);
     return LOBPCG_OK;
 }

@@ -8,6 +8,7 @@
 //                (Gram blocks of eq. go and of Cholesky-QR, Section 3.4),
 //                accumulated in FP64 across row runs
 //   k_combine    Z_o = [A_0 .. A_{na-1}] C_o for up to two outputs sharing
+//   k_combine_reg  the same for float32 and k in {8, 16, 20}, C in registers
 //                the inputs (eqs. xupd, pupd, upd1, upd2; W <- W - X B;
 //                W <- W R^{-1}), in place by rows
 //   k_small_*    one-CTA FP64 kernels on the k x k / 3k x 3k matrices:
@@ -36,7 +37,8 @@ __device__ __forceinline__ double guard_pivot(double t, double theta) {
 }
 
 // One thread per element of the n x k block; blockDim is a multiple of k, so
-// a thread keeps one column.  norms[j] += ||r_j||^2, norms[k + j] += ||x_j||^2.
+// a thread keeps one column.  norms[j] += ||r_j||^2, norms[k + j] += ||x_j||^2
+// (each thread sums its share in T, then FP64 across threads).
 // mode 0: W = R; mode 1: W = R / g(d - theta) (diagonal preconditioner).
 template <typename T>
 __global__ void k_resid(int64_t n, int k, const T *X, const T *HX, const double *theta, const float *d, T *W,
@@ -47,22 +49,27 @@ __global__ void k_resid(int64_t n, int k, const T *X, const T *HX, const double 
     const bool active = threadIdx.x < per * k;
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) red[q] = 0.0;
     __syncthreads();
-    double rr = 0.0, xx = 0.0;
-    const double th = theta[j];
+    T rr = T(0), xx = T(0);
+    const T th = static_cast<T>(theta[j]);
+    const T delta = static_cast<T>(1e-3) * (fabs(th) > T(1) ? fabs(th) : T(1));
     if (active) {
         const int64_t stride = static_cast<int64_t>(gridDim.x) * per;
         for (int64_t i = static_cast<int64_t>(blockIdx.x) * per + threadIdx.x / k; i < n; i += stride) {
             const int64_t e = i * k + j;
-            const double x = static_cast<double>(X[e]);
-            const double r = static_cast<double>(HX[e]) - x * th;
-            rr += r * r;
-            xx += x * x;
-            double w = r;
-            if (mode == 1) w = r / guard_pivot(static_cast<double>(d[i]) - th, th);
-            W[e] = static_cast<T>(w);
+            const T x = X[e];
+            const T r = HX[e] - x * th;
+            rr = fma(r, r, rr);
+            xx = fma(x, x, xx);
+            T w = r;
+            if (mode == 1) {
+                const T t = static_cast<T>(d[i]) - th;   // guarded shifted pivot g(t)
+                const T g = (t >= T(0)) ? (t > delta ? t : delta) : (-t > delta ? t : -delta);
+                w = r / g;
+            }
+            W[e] = w;
         }
-        atomicAdd(&red[j], rr);
-        atomicAdd(&red[k + j], xx);
+        atomicAdd(&red[j], static_cast<double>(rr));
+        atomicAdd(&red[k + j], static_cast<double>(xx));
     }
     __syncthreads();
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) atomicAdd(&norms[q], red[q]);
@@ -73,36 +80,68 @@ __global__ void k_resid(int64_t n, int k, const T *X, const T *HX, const double 
 constexpr int GR_ROWS = 64;     // rows staged per pass
 constexpr int GR_THREADS = 256; // 16 x 16 thread grid over the output
 
+// Copy rows [r0, r0 + rows) of an n x k block (one contiguous run of rows*k
+// values) into shared memory, zero-filling up to nrows rows; 16-byte vector
+// loads when k*sizeof(T) is a multiple of 16.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *dst, const T *src, int64_t r0, int rows, int nrows, int k) {
+    const int total = nrows * k, valid = rows * k;
+    constexpr int V = 16 / sizeof(T);
+    const T *s0 = src + r0 * k;
+    if ((k % V) == 0 && (reinterpret_cast<uintptr_t>(s0) & 15u) == 0) {
+        for (int e = threadIdx.x * V; e < total; e += blockDim.x * V) {
+            if (e < valid) {
+                *reinterpret_cast<float4 *>(dst + e) = __ldg(reinterpret_cast<const float4 *>(s0 + e));
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; ++q) dst[e + q] = T(0);
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = (e < valid) ? s0[e] : T(0);
+    }
+}
+
 // M (ma x mb, FP64, row-major, pre-zeroed) += A^T B.  A = [A_0..A_{na-1}],
-// B = [B_0..B_{nb-1}], each block n x k.  Thread (tx, ty) owns the outputs
-// (tx + 16u, ty + 16v), u < UA, v < UB.  Products are summed in T over one
-// staged run of GR_ROWS rows, then added to FP64 accumulators.
+// B = [B_0..B_{nb-1}], each block n x k, staged per block (tile of GR_ROWS
+// rows, row stride k).  Thread (tx, ty) owns the outputs (tx + 16u, ty + 16v),
+// u < UA, v < UB.  Products are summed in T over one staged tile, then added
+// to FP64 accumulators.
 template <typename T, int UA, int UB>
 __global__ void __launch_bounds__(GR_THREADS) k_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb,
                                                      GemmBlocks<T> b, double *M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ma = na * k, mb = nb * k;
-    T *sa = reinterpret_cast<T *>(smem_raw);   // [GR_ROWS][ma]
-    T *sb = sa + GR_ROWS * ma;                 // [GR_ROWS][mb]
+    T *sa = reinterpret_cast<T *>(smem_raw);   // na tiles [GR_ROWS][k]
+    T *sb = sa + na * GR_ROWS * k;             // nb tiles [GR_ROWS][k]
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[UA][UB];
+    // per-output base pointers into the staged tiles
+    const T *pa[UA];
+    const T *pb[UB];
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+        const int ia = min(tx + 16 * u, ma - 1);
+        pa[u] = sa + (ia / k) * GR_ROWS * k + ia % k;
+    }
+#pragma unroll
+    for (int v = 0; v < UB; ++v) {
+        const int ib = min(ty + 16 * v, mb - 1);
+        pb[v] = sb + (ib / k) * GR_ROWS * k + ib % k;
+    }
+    // Accumulation across tiles in T with Kahan compensation (cheap FP32 adds;
+    // the FP64 pipe is reserved for the final reduction across blocks).
+    T acc[UA][UB], cmp[UA][UB];
 #pragma unroll
     for (int u = 0; u < UA; ++u)
 #pragma unroll
-        for (int v = 0; v < UB; ++v) acc[u][v] = 0.0;
+        for (int v = 0; v < UB; ++v) acc[u][v] = cmp[u][v] = T(0);
     const int64_t ntile = (n + GR_ROWS - 1) / GR_ROWS;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const int64_t r0 = tile * GR_ROWS;
         const int rows = static_cast<int>(n - r0 < GR_ROWS ? n - r0 : GR_ROWS);
         __syncthreads();
-        for (int e = threadIdx.x; e < GR_ROWS * ma; e += blockDim.x) {
-            const int r = e / ma, c = e % ma, blk = c / k, cc = c % k;
-            sa[e] = (r < rows) ? a.p[blk][(r0 + r) * k + cc] : T(0);
-        }
-        for (int e = threadIdx.x; e < GR_ROWS * mb; e += blockDim.x) {
-            const int r = e / mb, c = e % mb, blk = c / k, cc = c % k;
-            sb[e] = (r < rows) ? b.p[blk][(r0 + r) * k + cc] : T(0);
-        }
+        for (int q = 0; q < na; ++q) stage_rows<T>(sa + q * GR_ROWS * k, a.p[q], r0, rows, GR_ROWS, k);
+        for (int q = 0; q < nb; ++q) stage_rows<T>(sb + q * GR_ROWS * k, b.p[q], r0, rows, GR_ROWS, k);
         __syncthreads();
         T part[UA][UB];
 #pragma unroll
@@ -112,15 +151,9 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram(int64_t n, int k, int na, G
         for (int r = 0; r < rows; ++r) {
             T av[UA], bv[UB];
 #pragma unroll
-            for (int u = 0; u < UA; ++u) {
-                const int ia = tx + 16 * u;
-                av[u] = ia < ma ? sa[r * ma + ia] : T(0);
-            }
+            for (int u = 0; u < UA; ++u) av[u] = pa[u][r * k];
 #pragma unroll
-            for (int v = 0; v < UB; ++v) {
-                const int ib = ty + 16 * v;
-                bv[v] = ib < mb ? sb[r * mb + ib] : T(0);
-            }
+            for (int v = 0; v < UB; ++v) bv[v] = pb[v][r * k];
 #pragma unroll
             for (int u = 0; u < UA; ++u)
 #pragma unroll
@@ -129,14 +162,20 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram(int64_t n, int k, int na, G
 #pragma unroll
         for (int u = 0; u < UA; ++u)
 #pragma unroll
-            for (int v = 0; v < UB; ++v) acc[u][v] += static_cast<double>(part[u][v]);
+            for (int v = 0; v < UB; ++v) {
+                const T y = part[u][v] - cmp[u][v];
+                const T t = acc[u][v] + y;
+                cmp[u][v] = (t - acc[u][v]) - y;
+                acc[u][v] = t;
+            }
     }
 #pragma unroll
     for (int u = 0; u < UA; ++u)
 #pragma unroll
         for (int v = 0; v < UB; ++v) {
             const int ia = tx + 16 * u, ib = ty + 16 * v;
-            if (ia < ma && ib < mb) atomicAdd(&M[ia * mb + ib], acc[u][v]);
+            if (ia < ma && ib < mb)
+                atomicAdd(&M[ia * mb + ib], static_cast<double>(acc[u][v]) - static_cast<double>(cmp[u][v]));
         }
 }
 
@@ -154,89 +193,191 @@ __device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
 
 constexpr int CB_ROWS = 32;
 
-// For up to two outputs: Z_o[i, :] = sum_c A[i, c0_o + c] C_o[c, :] over the
-// staged rows of A = [A_0..A_{na-1}] (columns c0_o .. ma-1); C_o is
-// (ma - c0_o) x k FP64, staged transposed (and zero-padded to 4 columns) in
-// T.  Thread (row, j) walks c in steps of 4 with 16-byte shared loads.  Rows
-// are staged before any output is written, so outputs may alias inputs.
+// For up to two outputs: Z_o[i, :] = sum_c A[i, c] C_o[c - c0_o, :] over
+// columns c >= c0_o of A = [A_0..A_{na-1}]; C_o is (ma - c0_o) x k FP64,
+// staged transposed in T.  A is staged per block (tile of CB_ROWS rows, row
+// stride k).  Thread (row, j) of a pass; blockDim is a multiple of k, so a
+// thread keeps column j and sums ||z_j||^2 for the output norm_of in FP64,
+// reduced per block before one global atomic per column.  Rows are staged
+// before any output is written, so outputs may alias inputs.
 template <typename T>
 __global__ void k_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out,
                           double *colsq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ma = na * k;
-    const int ma4 = (ma + 3) & ~3;
-    T *sa = reinterpret_cast<T *>(smem_raw);       // [CB_ROWS][ma4]
-    T *sc = sa + CB_ROWS * ma4;                    // [2][k][ma4]  (C transposed)
+    const int ms = ma | 1;                         // odd row stride of C^T: conflict-free column reads
+    T *sa = reinterpret_cast<T *>(smem_raw);       // na tiles [CB_ROWS][k]
+    T *sc = sa + na * CB_ROWS * k;                 // [2][k][ms]  (C transposed)
+    double *red = reinterpret_cast<double *>(sc + 2 * k * ms + 2);   // [k]
+    red = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(red) + 15) & ~uintptr_t(15));
     for (int o = 0; o < nout; ++o) {
         const int c0 = out.c0[o];
-        for (int e = threadIdx.x; e < k * ma4; e += blockDim.x) {
-            const int j = e / ma4, c = e % ma4;
-            sc[o * k * ma4 + e] = (c >= c0 && c < ma) ? static_cast<T>(out.C[o][(c - c0) * k + j]) : T(0);
+        for (int e = threadIdx.x; e < k * ma; e += blockDim.x) {
+            const int j = e / ma, c = e % ma;
+            sc[o * k * ms + j * ms + c] = (c >= c0) ? static_cast<T>(out.C[o][(c - c0) * k + j]) : T(0);
         }
     }
+    for (int j = threadIdx.x; j < k; j += blockDim.x) red[j] = 0.0;
+    const int per = blockDim.x / k;
+    const int j = threadIdx.x % k, rr = threadIdx.x / k;
+    const bool act = threadIdx.x < per * k;
+    double nsq = 0.0;
     const int64_t ntile = (n + CB_ROWS - 1) / CB_ROWS;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const int64_t r0 = tile * CB_ROWS;
         const int rows = static_cast<int>(n - r0 < CB_ROWS ? n - r0 : CB_ROWS);
         __syncthreads();
-        for (int e = threadIdx.x; e < CB_ROWS * ma4; e += blockDim.x) {
-            const int r = e / ma4, c = e % ma4;
-            T v = T(0);
-            if (r < rows && c < ma) v = a.p[c / k][(r0 + r) * k + c % k];
-            sa[e] = v;
-        }
+        for (int q = 0; q < na; ++q) stage_rows<T>(sa + q * CB_ROWS * k, a.p[q], r0, rows, CB_ROWS, k);
         __syncthreads();
+        if (!act) continue;
         for (int o = 0; o < nout; ++o) {
-            const int cstart = out.c0[o] & ~3;
-            const T *ct = sc + o * k * ma4;
-            for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
-                const int r = e / k, j = e % k;
-                const T *ar = sa + r * ma4;
-                const T *cr = ct + j * ma4;
-                T s = T(0);
-                for (int c = cstart; c < ma4; c += 4) {
-                    T x[4], y[4];
-                    load4(ar + c, x);
-                    load4(cr + c, y);
-                    s = fma(x[0], y[0], s);
-                    s = fma(x[1], y[1], s);
-                    s = fma(x[2], y[2], s);
-                    s = fma(x[3], y[3], s);
+            const T *ct = sc + o * k * ms + j * ms;
+            const int c0 = out.c0[o];
+            for (int r = rr; r < rows; r += 2 * per) {   // two rows per thread: two independent chains
+                const int r2 = r + per;
+                const bool two = r2 < rows;
+                T s = T(0), s2 = T(0);
+                for (int q = c0 / k; q < na; ++q) {   // c0 is 0 or k
+                    const T *arow = sa + q * CB_ROWS * k + r * k;
+                    const T *arow2 = sa + q * CB_ROWS * k + (two ? r2 : r) * k;
+                    const T *cq = ct + q * k;
+                    for (int cc = 0; cc < k; ++cc) {
+                        const T cv = cq[cc];
+                        s = fma(arow[cc], cv, s);
+                        s2 = fma(arow2[cc], cv, s2);
+                    }
                 }
                 out.z[o][(r0 + r) * k + j] = s;
-                if (colsq && o == out.norm_of) atomicAdd(&colsq[j], static_cast<double>(s) * static_cast<double>(s));
+                if (o == out.norm_of) nsq += static_cast<double>(s) * static_cast<double>(s);
+                if (two) {
+                    out.z[o][(r0 + r2) * k + j] = s2;
+                    if (o == out.norm_of) nsq += static_cast<double>(s2) * static_cast<double>(s2);
+                }
             }
         }
+    }
+    if (colsq) {
+        __syncthreads();
+        if (act) atomicAdd(&red[j], nsq);
+        __syncthreads();
+        for (int q = threadIdx.x; q < k; q += blockDim.x) atomicAdd(&colsq[q], red[q]);
+    }
+}
+
+// Float copies of the combine coefficients: Cf[0..n0) = C0, Cf[n0..n0+n1) = C1
+// (row offsets as in the FP64 matrices; C1 placed after C0's full NA K x K).
+__global__ void k_coef_to_float(int n0, const double *C0, const double *C1, int n1, float *Cf) {
+    for (int e = threadIdx.x; e < n0; e += blockDim.x) Cf[e] = static_cast<float>(C0[e]);
+    if (C1)
+        for (int e = threadIdx.x; e < n1; e += blockDim.x) Cf[n0 + e] = static_cast<float>(C1[e]);
+}
+
+// float32, K in {8, 16, 20}: each thread keeps column j of both coefficient
+// matrices in registers and walks rows; the staged A row is read with
+// 16-byte broadcast loads (a row group of K threads reads the same row).
+// Output 1, when present, starts at block 1 (c0 = K).  Semantics as k_combine.
+template <int K, int NA>
+__global__ void __launch_bounds__(128) k_combine_reg(int64_t n, GemmBlocks<float> a, int nout, CombineOut<float> out,
+                                                     double *colsq) {
+    __shared__ __align__(16) float sa[NA * CB_ROWS * K];
+    __shared__ double red[K];
+    constexpr int G = 128 / K;   // row groups
+    const int j = threadIdx.x % K, grp = threadIdx.x / K;
+    const bool act = grp < G;
+    float c0[NA * K], c1[NA * K];
+#pragma unroll
+    for (int c = 0; c < NA * K; ++c) {
+        c0[c] = out.Cf[c * K + j];
+        c1[c] = (nout > 1 && c >= K) ? out.Cf[NA * K * K + (c - K) * K + j] : 0.f;
+    }
+    for (int q = threadIdx.x; q < K; q += blockDim.x) red[q] = 0.0;
+    double nsq = 0.0;
+    const int64_t ntile = (n + CB_ROWS - 1) / CB_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t r0 = tile * CB_ROWS;
+        const int rows = static_cast<int>(n - r0 < CB_ROWS ? n - r0 : CB_ROWS);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NA; ++q) stage_rows<float>(sa + q * CB_ROWS * K, a.p[q], r0, rows, CB_ROWS, K);
+        __syncthreads();
+        if (!act) continue;
+        for (int r = grp; r < rows; r += G) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < NA; ++q) {
+                const float4 *ar = reinterpret_cast<const float4 *>(sa + q * CB_ROWS * K + r * K);
+#pragma unroll
+                for (int c4 = 0; c4 < K / 4; ++c4) {
+                    const float4 v = ar[c4];
+                    const int c = q * K + 4 * c4;
+                    s0 = fmaf(v.x, c0[c], s0);
+                    s0 = fmaf(v.y, c0[c + 1], s0);
+                    s0 = fmaf(v.z, c0[c + 2], s0);
+                    s0 = fmaf(v.w, c0[c + 3], s0);
+                    if (q > 0) {
+                        s1 = fmaf(v.x, c1[c], s1);
+                        s1 = fmaf(v.y, c1[c + 1], s1);
+                        s1 = fmaf(v.z, c1[c + 2], s1);
+                        s1 = fmaf(v.w, c1[c + 3], s1);
+                    }
+                }
+            }
+            out.z[0][(r0 + r) * K + j] = s0;
+            if (out.norm_of == 0) nsq += static_cast<double>(s0) * s0;
+            if (nout > 1) {
+                out.z[1][(r0 + r) * K + j] = s1;
+                if (out.norm_of == 1) nsq += static_cast<double>(s1) * s1;
+            }
+        }
+    }
+    if (colsq) {
+        __syncthreads();
+        if (act) atomicAdd(&red[j], nsq);
+        __syncthreads();
+        for (int q = threadIdx.x; q < K; q += blockDim.x) atomicAdd(&colsq[q], red[q]);
     }
 }
 
 // ---------------------------------------------------------------- small FP64 (one CTA)
+
+constexpr int EIG_MAXM_TRI = 96;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // In-place Cholesky of the m x m matrix A (lower triangle used), row-major in
 // shared memory.  Returns false if a pivot is not > 0 or the pivots span more
 // than `span` (max L_jj / min L_jj).
 __device__ bool cta_cholesky(double *A, int m, double span) {
     __shared__ int ok;
-    __shared__ double dmin, dmax;
+    __shared__ double dmin, dmax, rl;
     if (threadIdx.x == 0) { ok = 1; dmin = 1e300; dmax = 0.0; }
     __syncthreads();
+    // right-looking: after step j, column j holds L and the trailing block its Schur complement
     for (int j = 0; j < m; ++j) {
         if (threadIdx.x == 0) {
-            double s = A[j * m + j];
-            for (int p = 0; p < j; ++p) s -= A[j * m + p] * A[j * m + p];
-            if (!(s > 0.0)) ok = 0;
-            const double l = ok ? sqrt(s) : 1.0;
-            A[j * m + j] = l;
-            dmin = fmin(dmin, l);
-            dmax = fmax(dmax, l);
+            const double s = A[j * m + j];
+            if (!(s > 0.0)) {
+                ok = 0;
+            } else {
+                const double l = sqrt(s);
+                A[j * m + j] = l;
+                rl = 1.0 / l;
+                dmin = fmin(dmin, l);
+                dmax = fmax(dmax, l);
+            }
         }
         __syncthreads();
         if (!ok) return false;
-        const double ljj = A[j * m + j];
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-            double t = A[i * m + j];
-            for (int p = 0; p < j; ++p) t -= A[i * m + p] * A[j * m + p];
-            A[i * m + j] = t / ljj;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= rl;
+        __syncthreads();
+        const int nt = m - j - 1;
+        for (int q = threadIdx.x; q < nt * nt; q += blockDim.x) {
+            const int i = j + 1 + q / nt, l = j + 1 + q % nt;
+            if (l <= i) A[i * m + l] -= A[i * m + j] * A[l * m + j];
         }
         __syncthreads();
     }
@@ -251,12 +392,15 @@ __device__ bool cta_cholesky(double *A, int m, double span) {
 // Li = L^{-1} for lower-triangular L (m x m, shared memory): column j by
 // forward substitution, one thread per column.
 __device__ void cta_tri_inverse(const double *L, double *Li, int m) {
+    __shared__ double rdiag[EIG_MAXM_TRI];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) rdiag[i] = 1.0 / L[i * m + i];
+    __syncthreads();
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         for (int i = 0; i < m; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
             if (i < j) { Li[i * m + j] = 0.0; continue; }
+            double s = (i == j) ? 1.0 : 0.0;
             for (int p = j; p < i; ++p) s -= L[i * m + p] * Li[p * m + j];
-            Li[i * m + j] = s / L[i * m + i];
+            Li[i * m + j] = s * rdiag[i];
         }
     }
     __syncthreads();
@@ -299,7 +443,7 @@ __device__ int cta_jacobi(double *A, double *V, int m, double *cs, int *pairs, i
             off = sqrt(o);
         }
         __syncthreads();
-        if (off <= 1e-15 * fro || off == 0.0) return sweep;
+        if (off <= 1e-14 * fro || off == 0.0) return sweep;
         for (int round = 0; round < mm - 1; ++round) {
             // round-robin: position 0 fixed, the others rotate
             for (int t = threadIdx.x; t < mm / 2; t += blockDim.x) {
@@ -366,29 +510,285 @@ __device__ int cta_jacobi(double *A, double *V, int m, double *cs, int *pairs, i
         off = sqrt(o);
     }
     __syncthreads();
-    return (off <= 1e-15 * fro || off == 0.0) ? max_sweeps : -1;
+    return (off <= 1e-13 * fro || off == 0.0) ? max_sweeps : -1;
+}
+
+// The k smallest eigenpairs of the symmetric m x m matrix A (shared memory,
+// destroyed), FP64, one CTA (m <= 96, k <= 32):
+//   1. Householder tridiagonalisation A = Q T Q^T (Golub & Van Loan,
+//      Section 8.3.1); the reflectors stay in A's lower triangle.
+//   2. Eigenvalue i of T by bisection on the Sturm count (the number of
+//      negative pivots of T - x I), one thread per eigenvalue.
+//   3. Its eigenvector by inverse iteration: tridiagonal LU with partial
+//      pivoting of T - w_i I, three solves from distinct start vectors.
+//      Vectors of eigenvalues closer than 1e-10 ||T|| are re-orthogonalised.
+//   4. Back-transformation by the reflectors: V = Q Y.
+// Outputs: w[0..k) ascending, V (m x k, row-major, shared memory).
+constexpr int EIG_MAXM = 96;
+
+__device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V, double *d, double *e,
+                                  double *tau, double *pv) {
+    __shared__ double red_s, tnorm;
+    // 1. tridiagonalisation (reductions by warps, updates by all threads)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    __shared__ double kk_s;
+    for (int j = 0; j + 2 < m; ++j) {
+        if (warp == 0) {
+            double sg = 0.0;
+            for (int i = j + 2 + lane; i < m; i += 32) sg += A[i * m + j] * A[i * m + j];
+            sg = warp_sum_d(sg);
+            if (lane == 0) {
+                const double x0 = A[(j + 1) * m + j];
+                if (sg == 0.0) {
+                    tau[j] = 0.0;
+                    e[j] = x0;
+                    red_s = 0.0;
+                } else {
+                    const double mu = sqrt(x0 * x0 + sg);
+                    const double alpha = (x0 <= 0.0) ? mu : -mu;   // reflect onto -sign(x0) ||x|| e_1
+                    const double v0 = x0 - alpha;
+                    tau[j] = 2.0 * v0 * v0 / (sg + v0 * v0);
+                    red_s = 1.0 / v0;
+                    e[j] = alpha;
+                }
+                A[(j + 1) * m + j] = 1.0;   // v_0 = 1
+                d[j] = A[j * m + j];
+            }
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
+        for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= red_s;
+        __syncthreads();
+        // p = tau A22 v: one warp per row
+        for (int i = j + 1 + warp; i < m; i += nwarps) {
+            double acc = 0.0;
+            for (int l = j + 1 + lane; l < m; l += 32) acc += A[i * m + l] * A[l * m + j];
+            acc = warp_sum_d(acc);
+            if (lane == 0) pv[i] = tj * acc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double kk = 0.0;
+            for (int l = j + 1 + lane; l < m; l += 32) kk += A[l * m + j] * pv[l];
+            kk = warp_sum_d(kk);
+            if (lane == 0) kk_s = 0.5 * tj * kk;
+        }
+        __syncthreads();
+        // A22 -= v w^T + w v^T with w = p - K v
+        const int mm = m - j - 1;
+        const double K = kk_s;
+        for (int q = threadIdx.x; q < mm * mm; q += blockDim.x) {
+            const int i = j + 1 + q / mm, l = j + 1 + q % mm;
+            const double vi = A[i * m + j], vl = A[l * m + j];
+            A[i * m + l] -= vi * (pv[l] - K * vl) + (pv[i] - K * vi) * vl;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (m >= 2) {
+            d[m - 2] = A[(m - 2) * m + (m - 2)];
+            e[m - 2] = A[(m - 1) * m + (m - 2)];
+            if (m >= 3) tau[m - 2] = 0.0;
+        }
+        d[m - 1] = A[(m - 1) * m + (m - 1)];
+        double tn = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+            tn = fmax(tn, r);
+        }
+        tnorm = tn;
+    }
+    __syncthreads();
+    // 2. eigenvalue estimates by float32 multisection: one warp per wanted
+    //    eigenvalue, its 32 lanes count the eigenvalues below 32 points of the
+    //    current bracket (Sturm count = negative pivots of T - x I), so each
+    //    step narrows the bracket 33-fold.  Float32 counts are exact away
+    //    from an eigenvalue by more than ~m eps32 ||T||.
+    for (int i = warp; i < k; i += nwarps) {
+        float flo = static_cast<float>(-tnorm), fhi = static_cast<float>(tnorm);
+        for (int it = 0; it < 8 && fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f; ++it) {
+            const float x = flo + (fhi - flo) * static_cast<float>(lane + 1) / 33.f;
+            int cnt = 0;
+            float q = static_cast<float>(d[0]) - x;
+            cnt += q < 0.f;
+            for (int r = 1; r < m; ++r) {
+                if (fabsf(q) < 1e-30f) q = (q < 0.f) ? -1e-30f : 1e-30f;
+                const float er = static_cast<float>(e[r - 1]);
+                q = (static_cast<float>(d[r]) - x) - __fdividef(er * er, q);
+                cnt += q < 0.f;
+            }
+            // lanes whose point has more than i eigenvalues below it bound from above
+            const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
+            const int first = above ? (__ffs(above) - 1) : 32;    // first lane with cnt > i
+            const float nlo = (first == 0) ? flo : flo + (fhi - flo) * static_cast<float>(first) / 33.f;
+            const float nhi = (first == 32) ? fhi : flo + (fhi - flo) * static_cast<float>(first + 1) / 33.f;
+            flo = nlo;
+            fhi = nhi;
+        }
+        // float64 multisection from the float32 bracket, widened by the
+        // float32 count uncertainty; the pivot reciprocal is a float32 seed
+        // refined by one Newton step (relative error ~1e-14, enough for signs)
+        double lo = static_cast<double>(flo), hi = static_cast<double>(fhi);
+        const double pad = 1e-5 * tnorm + 1e-300;
+        lo = fmax(-tnorm, lo - pad);
+        hi = fmin(tnorm, hi + pad);
+        for (int it = 0; it < 12 && hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+            const double x = lo + (hi - lo) * static_cast<double>(lane + 1) / 33.0;
+            int cnt = 0;
+            double q = d[0] - x;
+            cnt += q < 0.0;
+            for (int r = 1; r < m; ++r) {
+                if (fabs(q) < 1e-280) q = (q < 0.0) ? -1e-280 : 1e-280;
+                double rc = static_cast<double>(__frcp_rn(static_cast<float>(q)));
+                if (!isfinite(rc)) rc = 1.0 / q;   // outside float range
+                rc = rc * (2.0 - q * rc);
+                q = (d[r] - x) - e[r - 1] * e[r - 1] * rc;
+                cnt += q < 0.0;
+            }
+            const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
+            const int first = above ? (__ffs(above) - 1) : 32;
+            const double nlo = (first == 0) ? lo : lo + (hi - lo) * static_cast<double>(first) / 33.0;
+            const double nhi = (first == 32) ? hi : lo + (hi - lo) * static_cast<double>(first + 1) / 33.0;
+            lo = nlo;
+            hi = nhi;
+        }
+        if (lane == 0) w[i] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    // 3. eigenvector by inverse iteration in float64, one thread per pair;
+    //    the Ritz value is then the Rayleigh quotient y^T T y.
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double tiny = 1e-300;
+        const double lam = w[i];
+        // inverse iteration: LU (partial pivoting) of T - lam I
+        double D[EIG_MAXM], DL[EIG_MAXM], DU[EIG_MAXM], DU2[EIG_MAXM], y[EIG_MAXM];
+        bool piv[EIG_MAXM];
+        const double pert = 2.2e-16 * tnorm + tiny;
+        for (int r = 0; r < m; ++r) {
+            D[r] = d[r] - lam;
+            DL[r] = (r + 1 < m) ? e[r] : 0.0;
+            DU[r] = (r + 1 < m) ? e[r] : 0.0;
+            DU2[r] = 0.0;
+            piv[r] = false;
+        }
+        for (int r = 0; r + 1 < m; ++r) {
+            if (fabs(D[r]) >= fabs(DL[r])) {
+                if (D[r] == 0.0) D[r] = pert;
+                const double f = DL[r] / D[r];
+                DL[r] = f;
+                D[r + 1] -= f * DU[r];
+            } else {
+                const double f = D[r] / DL[r];
+                D[r] = DL[r];
+                DL[r] = f;
+                const double t = DU[r];
+                DU[r] = D[r + 1];
+                D[r + 1] = t - f * D[r + 1];
+                if (r + 2 < m) {
+                    DU2[r] = DU[r + 1];
+                    DU[r + 1] = -f * DU[r + 1];
+                }
+                piv[r] = true;
+            }
+        }
+        if (D[m - 1] == 0.0) D[m - 1] = pert;
+        for (int r = 0; r < m; ++r) D[r] = 1.0 / D[r];   // reciprocal pivots
+        for (int r = 0; r < m; ++r) y[r] = 1.0 + 0.25 * static_cast<double>((r * 7 + i * 13) % 11) / 11.0;
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            for (int r = 0; r + 1 < m; ++r) {
+                if (!piv[r]) {
+                    y[r + 1] -= DL[r] * y[r];
+                } else {
+                    const double t = y[r];
+                    y[r] = y[r + 1];
+                    y[r + 1] = t - DL[r] * y[r];
+                }
+            }
+            y[m - 1] *= D[m - 1];
+            if (m >= 2) y[m - 2] = (y[m - 2] - DU[m - 2] * y[m - 1]) * D[m - 2];
+            for (int r = m - 3; r >= 0; --r) y[r] = (y[r] - DU[r] * y[r + 1] - DU2[r] * y[r + 2]) * D[r];
+            double nrm = 0.0;
+            for (int r = 0; r < m; ++r) nrm += y[r] * y[r];
+            nrm = 1.0 / sqrt(nrm);
+            for (int r = 0; r < m; ++r) y[r] *= nrm;
+        }
+        double rq = 0.0;
+        for (int r = 0; r < m; ++r) {
+            double ty = d[r] * y[r];
+            if (r > 0) ty += e[r - 1] * y[r - 1];
+            if (r + 1 < m) ty += e[r] * y[r + 1];
+            rq += y[r] * ty;
+        }
+        w[i] = rq;
+        for (int r = 0; r < m; ++r) V[r * k + i] = y[r];
+    }
+    __syncthreads();
+    // re-orthogonalise vectors of (nearly) equal eigenvalues, in order
+    for (int i = 1; i < k; ++i) {
+        for (int j2 = 0; j2 < i; ++j2) {
+            if (fabs(w[i] - w[j2]) > 1e-10 * tnorm) continue;
+            if (threadIdx.x == 0) {
+                double dot = 0.0;
+                for (int r = 0; r < m; ++r) dot += V[r * k + i] * V[r * k + j2];
+                red_s = dot;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] -= red_s * V[r * k + j2];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double nrm = 0.0;
+                for (int r = 0; r < m; ++r) nrm += V[r * k + i] * V[r * k + i];
+                red_s = 1.0 / sqrt(nrm);
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] *= red_s;
+            __syncthreads();
+        }
+    }
+    // 4. V = Q Y: apply the reflectors H_j = I - tau_j v_j v_j^T, last first
+    __shared__ double dots[32];
+    for (int j = m - 3; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
+        for (int c = warp; c < k; c += nwarps) {
+            double dot = 0.0;
+            for (int r = j + 1 + lane; r < m; r += 32) dot += A[r * m + j] * V[r * k + c];
+            dot = warp_sum_d(dot);
+            if (lane == 0) dots[c] = tj * dot;
+        }
+        __syncthreads();
+        const int rows = m - j - 1;
+        for (int q = threadIdx.x; q < rows * k; q += blockDim.x) {
+            const int r = j + 1 + q / k, c = q % k;
+            V[r * k + c] -= dots[c] * A[r * m + j];
+        }
+        __syncthreads();
+    }
 }
 
 // Rayleigh-Ritz on the pencil (G, O) of eq. rreig: keep the k leftmost pairs.
 // G, O: m x m FP64 (global).  pscale (may be null): scale of the last m - p0
 // rows/columns (the P block), applied as D G D, D O D and undone in C.
-//   1. Cholesky O = L L^T (pivots within a span of 1e7), G_hat = L^-1 G L^-T,
+//   1. Cholesky O = L L^T (pivots within a span of 1e4, i.e. cond(O) <= ~1e8),
+//      G_hat = L^-1 G L^-T,
 //      Jacobi G_hat = V D V^T, C = L^-T V[:, :k]
 //   2. if O is not numerically positive definite and p0 < m, drop the P
 //      block (m -> p0; C's P rows zero)
 //   3. if that fails too, go through O = U diag(s) U^T, dropping directions
-//      with s < 1e-12 s_max: C = U_r s_r^{-1/2} V[:, :k]
+//      with s < 1e-8 s_max: C = U_r s_r^{-1/2} V[:, :k]
 // Out: C (m x k), theta (k), status: 0 ok, 1 P dropped, 3 eigen route,
 // 2 breakdown (fewer than k directions left).
-__global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, const double *pscale,
+__global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, int ld, const double *pscale,
                                 double *Cout, double *theta, int *status) {
     extern __shared__ __align__(16) double sm[];
     double *sG = sm, *sO = sG + m * m, *sV = sO + m * m;
     __shared__ double cs[2 * 64];
     __shared__ int pairs[2 * 64];
     __shared__ double wsort[96], sig[96];
-    __shared__ int order[96];
+    __shared__ double tdd[EIG_MAXM], tee[EIG_MAXM], ttau[EIG_MAXM], tpv[EIG_MAXM];
     __shared__ int kept;
+    __shared__ double red_big;
     int mm = m;
     int st = 0;
     bool chol = false;
@@ -398,18 +798,18 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
             double si = 1.0, sj = 1.0;
             if (pscale && i >= p0) si = pscale[i - p0];
             if (pscale && j >= p0) sj = pscale[j - p0];
-            sG[e] = 0.5 * (G[i * m + j] + G[j * m + i]) * si * sj;
-            sO[e] = 0.5 * (O[i * m + j] + O[j * m + i]) * si * sj;
+            sG[e] = 0.5 * (G[i * ld + j] + G[j * ld + i]) * si * sj;
+            sO[e] = 0.5 * (O[i * ld + j] + O[j * ld + i]) * si * sj;
         }
         __syncthreads();
     };
     load(mm);
-    chol = cta_cholesky(sO, mm, 1e7);
+    chol = cta_cholesky(sO, mm, 1e4);
     if (!chol && p0 < m) {
         mm = p0;
         st = 1;
         load(mm);
-        chol = cta_cholesky(sO, mm, 1e7);
+        chol = cta_cholesky(sO, mm, 1e4);
     }
     if (chol) {
         // G_hat = L^{-1} G L^{-T}
@@ -423,26 +823,32 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
         st = 3;
         mm = m;
         load(mm);
-        cta_jacobi(sO, sV, mm, cs, pairs, 60);         // O = U diag(s) U^T, U in sV
+        cta_jacobi(sO, sV, mm, cs, pairs, 30);         // O = U diag(s) U^T, U in sV
         if (threadIdx.x == 0) {
             double smax = 0.0;
             for (int i = 0; i < mm; ++i) smax = fmax(smax, sO[i * mm + i]);
             int kc = 0;
             for (int i = 0; i < mm; ++i) {
                 const double si = sO[i * mm + i];
-                sig[i] = (si > 1e-12 * smax) ? 1.0 / sqrt(si) : 0.0;
-                kc += si > 1e-12 * smax;
+                sig[i] = (si > 1e-8 * smax) ? 1.0 / sqrt(si) : 0.0;
+                kc += si > 1e-8 * smax;
             }
             kept = kc;
         }
         __syncthreads();
         cta_matmul(sG, false, sV, false, sO, mm);      // sO = G U
         cta_matmul(sV, true, sO, false, sG, mm);       // sG = U^T G U
-        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sG[e] *= sig[e / mm] * sig[e % mm];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mx = 0.0;
+            for (int e = 0; e < mm * mm; ++e) mx = fmax(mx, fabs(sG[e]));
+            red_big = 4.0 * mm * mx + 1.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {   // dropped directions sort last
             const int i = e / mm, j = e % mm;
-            double v = sG[e] * sig[i] * sig[j];
-            if (sig[i] == 0.0 || sig[j] == 0.0) v = (i == j) ? 1e300 : 0.0;   // dropped directions sort last
-            sG[e] = v;
+            if (sig[i] == 0.0 || sig[j] == 0.0) sG[e] = (i == j) ? red_big : 0.0;
         }
         // scaled basis U s^{-1/2} into sO (plays the role of L^{-T}'s transpose below)
         __syncthreads();
@@ -465,30 +871,21 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
         }
     }
     __syncthreads();
-    const int sweeps = cta_jacobi(sG, sV, mm, cs, pairs, 60);
-    if (sweeps < 0 && st == 0) st = 4;
-    for (int i = threadIdx.x; i < mm; i += blockDim.x) wsort[i] = sG[i * mm + i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
-        int r = 0;
-        for (int j = 0; j < mm; ++j) r += (wsort[j] < wsort[i]) || (wsort[j] == wsort[i] && j < i);
-        order[r] = i;
-    }
-    __syncthreads();
-    // C = B V[:, order[0..k)] with B[i][p] = sO[p][i] (L^{-T}, or U s^{-1/2});
-    // rows of a dropped P block are zero; undo the P scaling
+    // k smallest eigenpairs of G_hat; eigenvectors (mm x k) into sV
+    cta_eigh_smallest(sG, mm, k, wsort, sV, tdd, tee, ttau, tpv);
+    // C = B Y with B[i][p] = sO[p][i] (L^{-T}, or U s^{-1/2}); rows of a
+    // dropped P block are zero; undo the P scaling
     const bool lower = chol;   // L^{-1} is lower triangular: B[i][p] = 0 for p < i
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
         double sacc = 0.0;
         if (i < mm) {
-            const int col = order[j];
-            for (int p = lower ? i : 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * mm + col];
+            for (int p = lower ? i : 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * k + j];
             if (pscale && i >= p0) sacc *= pscale[i - p0];
         }
         Cout[i * k + j] = sacc;
     }
-    for (int j = threadIdx.x; j < k; j += blockDim.x) theta[j] = wsort[order[j]];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) theta[j] = wsort[j];
     if (threadIdx.x == 0) *status = st;
 }
 
@@ -526,7 +923,7 @@ __global__ void k_orth_factor(int k, const double *B, double *Tout, int *status)
         return;
     }
     load();
-    cta_jacobi(sB, sL, k, cs, pairs, 60);
+    cta_jacobi(sB, sL, k, cs, pairs, 30);
     if (threadIdx.x == 0) {
         double mx = 0.0;
         for (int j = 0; j < k; ++j) mx = fmax(mx, sB[j * k + j]);
@@ -563,7 +960,7 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
     cudaError_t e = cudaMemsetAsync(M, 0, sizeof(double) * ma * mb, s);
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(T) * GR_ROWS * (ma + mb);
-    const int64_t ntile = (n + GR_ROWS - 1) / GR_ROWS;
+    const int64_t ntile = (n + GR_ROWS - 1) / GR_ROWS;   // one tile per block pass
     int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * 4));
     if (blocks < 1) blocks = 1;
     const int ua = (ma + 15) / 16, ub = (mb + 15) / 16;
@@ -575,10 +972,15 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
         return cudaGetLastError();                                                                            \
     }
     GRAM_CASE(1, 1)
+    GRAM_CASE(1, 2)
     GRAM_CASE(2, 2)
+    GRAM_CASE(2, 4)
     GRAM_CASE(3, 3)
+    GRAM_CASE(3, 6)
     GRAM_CASE(4, 4)
+    GRAM_CASE(4, 8)
     GRAM_CASE(6, 6)
+    GRAM_CASE(6, 12)
 #undef GRAM_CASE
     return cudaErrorInvalidValue;
 }
@@ -586,27 +988,45 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
 template <typename T>
 cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
                            int num_sms, cudaStream_t s) {
-    const int ma4 = (na * k + 3) & ~3;
-    const size_t smem = sizeof(T) * (CB_ROWS * ma4 + 2 * ma4 * k);
-    cudaError_t e = cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (colsq) {
         e = cudaMemsetAsync(colsq, 0, sizeof(double) * k, s);
         if (e != cudaSuccess) return e;
     }
     const int64_t ntile = (n + CB_ROWS - 1) / CB_ROWS;
+    if constexpr (std::is_same<T, float>::value) {
+        const bool reg_ok = (nout == 1 || out.c0[1] == k) && out.c0[0] == 0 && out.Cf != nullptr;
+        int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * 8));
+        if (blocks < 1) blocks = 1;
+#define COMBINE_REG(KK, NN)                                                                              \
+        if (reg_ok && k == KK && na == NN) {                                                             \
+            k_coef_to_float<<<1, 256, 0, s>>>(NN * KK * KK, out.C[0], nout > 1 ? out.C[1] : nullptr,   \
+                                               (NN - 1) * KK * KK, out.Cf);                              \
+            k_combine_reg<KK, NN><<<blocks, 128, 0, s>>>(n, a, nout, out, colsq);                        \
+            return cudaGetLastError();                                                                   \
+        }
+        COMBINE_REG(8, 1) COMBINE_REG(8, 2) COMBINE_REG(8, 3)
+        COMBINE_REG(16, 1) COMBINE_REG(16, 2) COMBINE_REG(16, 3)
+        COMBINE_REG(20, 1) COMBINE_REG(20, 2) COMBINE_REG(20, 3)
+#undef COMBINE_REG
+    }
+    const int ms = (na * k) | 1;
+    const size_t smem = sizeof(T) * (na * CB_ROWS * k + 2 * ms * k + 2) + sizeof(double) * (k + 2);
+    e = cudaFuncSetAttribute(k_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * 4));
     if (blocks < 1) blocks = 1;
-    k_combine<T><<<blocks, 256, smem, s>>>(n, k, na, a, nout, out, colsq);
+    const int threads = (256 / k) * k;
+    k_combine<T><<<blocks, threads, smem, s>>>(n, k, na, a, nout, out, colsq);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, const double *pscale,
+cudaError_t launch_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, int ld, const double *pscale,
                                  double *C, double *theta, int *status, cudaStream_t s) {
     const size_t smem = sizeof(double) * 3 * m * m;
     cudaError_t e = cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_rayleigh_ritz<<<1, 256, smem, s>>>(m, k, p0, G, O, pscale, C, theta, status);
+    k_rayleigh_ritz<<<1, 256, smem, s>>>(m, k, p0, G, O, ld, pscale, C, theta, status);
     return cudaGetLastError();
 }
 

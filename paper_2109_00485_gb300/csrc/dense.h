@@ -21,6 +21,7 @@ struct CombineOut {
     const double *C[2];
     int c0[2];
     int norm_of;
+    float *Cf = nullptr;   // device scratch (>= 2 * 96 * 32 floats) for float32 coefficient copies
 };
 
 template <typename T>
@@ -32,7 +33,9 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
 template <typename T>
 cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
                            int num_sms, cudaStream_t s);
-cudaError_t launch_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, const double *pscale,
+// G, O: m x m blocks with row stride ld (they may be the two halves of one
+// m x 2m Gram matrix).
+cudaError_t launch_rayleigh_ritz(int m, int k, int p0, const double *G, const double *O, int ld, const double *pscale,
                                  double *C, double *theta, int *status, cudaStream_t s);
 cudaError_t launch_orth_factor(int k, const double *B, double *T, int *status, cudaStream_t s);
 

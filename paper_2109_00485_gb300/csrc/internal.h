@@ -87,5 +87,7 @@ void solver_release(lobpcg_ctx *h);
 lobpcg_status solve(lobpcg_ctx *h, float *X, bool x_on_host, double *evals, double *resid, lobpcg_stats *st,
                     std::string &err);
 cudaError_t copy_x_f64(lobpcg_ctx *h, double *out);
+lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps, double *theta_out,
+                      lobpcg_stats *st, std::string &err);
 
 }  // namespace lobpcg

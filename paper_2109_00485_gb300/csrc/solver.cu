@@ -41,8 +41,13 @@ struct SolverState {
     Blocks<double> d;
     double *G = nullptr, *O = nullptr, *C = nullptr, *theta = nullptr, *norms = nullptr, *colsqP = nullptr;
     double *pscale = nullptr, *B = nullptr, *Tm = nullptr, *Cproj = nullptr;
+    float *Cf = nullptr;         // float copies of combine coefficients
     int *status = nullptr;       // [0] RR status, [1] orthonormalisation status
     double *h_buf = nullptr;     // pinned: norms (2k), theta (k), status (2 as doubles)
+    bool hasP32 = false;         // lobpcg_iterate: P holds a search direction
+    bool ready32 = false;        // lobpcg_iterate: state initialised
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the SpMM of an iteration
+    bool ev_pending = false;
 };
 
 __global__ void k_proj_coef(int k, const double *B, double *Cp) {
@@ -87,6 +92,17 @@ cudaError_t spmm_T<double>(lobpcg_ctx *h, const double *X, double *Y, int k) {
     return launch_spmm_sym_f64(h, X, Y, k, h->stream);
 }
 
+// H W with CUDA events around it on the handle's stream; the elapsed time is
+// collected at the next synchronisation (read_progress).
+template <typename T>
+cudaError_t timed_spmm(lobpcg_ctx *h, SolverState *s, const T *W, T *HW, int k) {
+    CK(cudaEventRecord(s->ev0, h->stream));
+    CK(spmm_T<T>(h, W, HW, k));
+    CK(cudaEventRecord(s->ev1, h->stream));
+    s->ev_pending = true;
+    return cudaSuccess;
+}
+
 template <typename T>
 Blocks<T> &blocks_of(SolverState *s);
 template <>
@@ -105,13 +121,22 @@ struct PhaseResult {
 // Read norms + theta + statuses (one sync); compute rho on the host.
 template <typename T>
 cudaError_t read_progress(lobpcg_ctx *h, SolverState *s, std::vector<double> &rho, std::vector<double> &theta,
-                          int *rr_status, int *orth_status) {
+                          int *rr_status, int *orth_status, lobpcg_stats *st) {
     const int k = s->k;
     CK(cudaMemcpyAsync(s->h_buf, s->norms, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(s->h_buf + 2 * k, s->theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(reinterpret_cast<int *>(s->h_buf + 3 * k), s->status, sizeof(int) * 2, cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (s->ev_pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+        if (st) {
+            st->spmm_ms += ms;
+            st->spmm_calls += 1;
+        }
+        s->ev_pending = false;
+    }
     rho.resize(k);
     theta.resize(k);
     const double G = h->gershgorin;
@@ -122,9 +147,9 @@ cudaError_t read_progress(lobpcg_ctx *h, SolverState *s, std::vector<double> &rh
         const double den = (h->params.resid_mode == 0) ? std::max(std::fabs(th), 1e-12 * G) * xn : G * xn;
         rho[j] = den > 0 ? rn / den : INFINITY;
     }
-    const int *st = reinterpret_cast<const int *>(s->h_buf + 3 * k);
-    *rr_status = st[0];
-    *orth_status = st[1];
+    const int *sts = reinterpret_cast<const int *>(s->h_buf + 3 * k);
+    *rr_status = sts[0];
+    *orth_status = sts[1];
     return cudaSuccess;
 }
 
@@ -144,12 +169,12 @@ cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     awx.p[0] = b.W;
     awx.p[1] = b.X;
     CombineOut<T> o1{};
-    o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1;
+    o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1; o1.Cf = s->Cf;
     CK(launch_combine<T>(n, k, 2, awx, 1, o1, nullptr, h->num_sms, h->stream));   // W -= X B
     CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream));          // B = W^T W
     CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
     CombineOut<T> o2{};
-    o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1;
+    o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1; o2.Cf = s->Cf;
     return launch_combine<T>(n, k, 1, aw, 1, o2, nullptr, h->num_sms, h->stream);  // W <- W T
 }
 
@@ -161,14 +186,60 @@ cudaError_t rr_on_x(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     GemmBlocks<T> ax{}, ahx{};
     ax.p[0] = b.X;
     ahx.p[0] = b.HX;
-    CK(launch_gram<T>(n, k, 1, ax, 1, ahx, s->G, h->num_sms, h->stream));
-    CK(launch_gram<T>(n, k, 1, ax, 1, ax, s->O, h->num_sms, h->stream));
-    CK(launch_rayleigh_ritz(k, k, k, s->G, s->O, nullptr, s->C, s->theta, s->status, h->stream));
+    GemmBlocks<T> ab{};
+    ab.p[0] = b.HX;
+    ab.p[1] = b.X;
+    CK(launch_gram<T>(n, k, 1, ax, 2, ab, s->G, h->num_sms, h->stream));   // [X^T HX | X^T X]
+    CK(launch_rayleigh_ritz(k, k, k, s->G, s->G + k, 2 * k, nullptr, s->C, s->theta, s->status, h->stream));
     CombineOut<T> ox{}, oh{};
-    ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0; ox.norm_of = -1;
-    oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0; oh.norm_of = -1;
+    ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0; ox.norm_of = -1; ox.Cf = s->Cf;
+    oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0; oh.norm_of = -1; oh.Cf = s->Cf;
     CK(launch_combine<T>(n, k, 1, ax, 1, ox, nullptr, h->num_sms, h->stream));
     return launch_combine<T>(n, k, 1, ahx, 1, oh, nullptr, h->num_sms, h->stream);
+}
+
+// Everything of one iteration after the residual (W = K^{-1} R in b.W):
+// preconditioner, orthonormalisation, H W, Gram, Rayleigh-Ritz, update.
+template <typename T>
+cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    const int pmode = h->params.precond;
+        // preconditioner (the diagonal one was applied inside the residual kernel)
+        if (pmode == 2) CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
+        // orthonormalise W against X and itself
+        CK(orth_pass<T>(h, s, b));
+        CK(orth_pass<T>(h, s, b));
+        // the one SpMM per iteration
+        CK(timed_spmm<T>(h, s, b.W, b.HW, k));
+        // Gram matrices of S = [X W P], HS = [HX HW HP]
+        const int na = hasP ? 3 : 2;
+        const int m = na * k;
+        GemmBlocks<T> aS{}, aHS{}, aB{};
+        aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
+        aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
+        for (int q = 0; q < na; ++q) {
+            aB.p[q] = aHS.p[q];
+            aB.p[na + q] = aS.p[q];
+        }
+        CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream));   // [S^T HS | S^T S]
+        if (hasP) {
+            k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
+            CK(cudaGetLastError());
+        }
+        CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->G + m, 2 * m, hasP ? s->pscale : nullptr, s->C, s->theta,
+                                s->status, h->stream));
+        // X = S C, P = [W P] C_23 (with ||p_j||^2), HX = HS C, HP = [HW HP] C_23
+        CombineOut<T> ox{}, oh{};
+        ox.Cf = s->Cf;
+        oh.Cf = s->Cf;
+        ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0;
+        ox.z[1] = b.P; ox.C[1] = s->C + static_cast<int64_t>(k) * k; ox.c0[1] = k; ox.norm_of = 1;
+        oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0;
+        oh.z[1] = b.HP; oh.C[1] = s->C + static_cast<int64_t>(k) * k; oh.c0[1] = k; oh.norm_of = -1;
+        CK(launch_combine<T>(n, k, na, aS, 2, ox, s->colsqP, h->num_sms, h->stream));
+        CK(launch_combine<T>(n, k, na, aHS, 2, oh, nullptr, h->num_sms, h->stream));
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -193,7 +264,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
         CK(launch_resid<T>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
                            h->stream));
         int rr_st = 0, orth_st = 0;
-        CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st));
+        CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
         if (rr_st == 2) {
             status = LOBPCG_ERR_BREAKDOWN;
             break;
@@ -213,7 +284,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
             CK(spmm_T<T>(h, b.X, b.HW, k));
             CK(launch_resid<T>(n, k, b.X, b.HW, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms,
                                h->num_sms, h->stream));
-            CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st));
+            CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
             double worst_e = 0.0;
             for (int j = 0; j < nev; ++j) worst_e = std::max(worst_e, rho[j]);
             if (worst_e <= tol || restarts >= 5) {
@@ -234,35 +305,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
         }
         if (res.iters >= max_iters) break;
         ++res.iters;
-        // preconditioner (the diagonal one was applied inside the residual kernel)
-        if (pmode == 2) CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
-        // orthonormalise W against X and itself
-        CK(orth_pass<T>(h, s, b));
-        CK(orth_pass<T>(h, s, b));
-        // the one SpMM per iteration
-        CK(spmm_T<T>(h, b.W, b.HW, k));
-        // Gram matrices of S = [X W P], HS = [HX HW HP]
-        const int na = hasP ? 3 : 2;
-        const int m = na * k;
-        GemmBlocks<T> aS{}, aHS{};
-        aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
-        aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
-        CK(launch_gram<T>(n, k, na, aS, na, aHS, s->G, h->num_sms, h->stream));
-        CK(launch_gram<T>(n, k, na, aS, na, aS, s->O, h->num_sms, h->stream));
-        if (hasP) {
-            k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
-            CK(cudaGetLastError());
-        }
-        CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->O, hasP ? s->pscale : nullptr, s->C, s->theta, s->status,
-                                h->stream));
-        // X = S C, P = [W P] C_23 (with ||p_j||^2), HX = HS C, HP = [HW HP] C_23
-        CombineOut<T> ox{}, oh{};
-        ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0;
-        ox.z[1] = b.P; ox.C[1] = s->C + static_cast<int64_t>(k) * k; ox.c0[1] = k; ox.norm_of = 1;
-        oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0;
-        oh.z[1] = b.HP; oh.C[1] = s->C + static_cast<int64_t>(k) * k; oh.c0[1] = k; oh.norm_of = -1;
-        CK(launch_combine<T>(n, k, na, aS, 2, ox, s->colsqP, h->num_sms, h->stream));
-        CK(launch_combine<T>(n, k, na, aHS, 2, oh, nullptr, h->num_sms, h->stream));
+        CK(iteration_body<T>(h, s, b, hasP));
         hasP = true;
     }
     res.rho = rho;
@@ -289,7 +332,7 @@ cudaError_t solver_setup(lobpcg_ctx *h) {
     CK(alloc_blocks<float>(h, s->f, k));
     if (h->params.polish_fp64) CK(alloc_blocks<double>(h, s->d, k));
     const int m = 3 * k;
-    CK(dev_alloc(h, reinterpret_cast<void **>(&s->G), sizeof(double) * m * m));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->G), sizeof(double) * 2 * m * m));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->O), sizeof(double) * m * m));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->C), sizeof(double) * m * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->theta), sizeof(double) * k));
@@ -300,14 +343,19 @@ cudaError_t solver_setup(lobpcg_ctx *h) {
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Tm), sizeof(double) * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cproj), sizeof(double) * 2 * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->status), sizeof(int) * 4));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cf), sizeof(float) * 2 * 96 * 32));
     CK(cudaMemsetAsync(s->status, 0, sizeof(int) * 4, h->stream));
     CK(cudaMallocHost(reinterpret_cast<void **>(&s->h_buf), sizeof(double) * (4 * k + 4)));
+    CK(cudaEventCreate(&s->ev0));
+    CK(cudaEventCreate(&s->ev1));
     return cudaSuccess;
 }
 
 void solver_release(lobpcg_ctx *h) {
     if (!h->solver) return;
     if (h->solver->h_buf) cudaFreeHost(h->solver->h_buf);
+    if (h->solver->ev0) cudaEventDestroy(h->solver->ev0);
+    if (h->solver->ev1) cudaEventDestroy(h->solver->ev1);
     delete h->solver;
     h->solver = nullptr;
 }
@@ -374,6 +422,57 @@ lobpcg_status solve(lobpcg_ctx *h, float *Xio, bool x_on_host, double *evals, do
         err = "maxiter reached before the residual tolerance";
         return LOBPCG_ERR_NOT_CONVERGED;
     }
+    return LOBPCG_OK;
+}
+
+// A fixed number of float32 iterations with no exit test (the residual
+// norms are still formed and read each iteration, as in the solve).  X0 (n x k,
+// device or host) starts a new run; NULL continues the previous one.
+lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps, double *theta_out,
+                      lobpcg_stats *st, std::string &err) {
+    SolverState *s = h->solver;
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    Blocks<float> &b = s->f;
+    auto fail = [&](cudaError_t e) {
+        err = std::string("iterate: ") + cudaGetErrorString(e);
+        return LOBPCG_ERR_CUDA;
+    };
+    auto t0 = std::chrono::steady_clock::now();
+    if (st) std::memset(st, 0, sizeof(*st));
+    cudaError_t e = cudaSuccess;
+    if (X0) {
+        e = cudaMemcpyAsync(b.X, X0, sizeof(float) * n * k, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            h->stream);
+        if (e == cudaSuccess) e = spmm_T<float>(h, b.X, b.HX, k);
+        if (e == cudaSuccess) e = rr_on_x<float>(h, s, b);
+        if (e != cudaSuccess) return fail(e);
+        s->hasP32 = false;
+        s->ready32 = true;
+    }
+    if (!s->ready32) {
+        err = "iterate: no state to continue (pass X0)";
+        return LOBPCG_ERR_ARG;
+    }
+    std::vector<double> rho, theta;
+    const int pmode = h->params.precond;
+    for (int it = 0; it < steps; ++it) {
+        e = launch_resid<float>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
+                                h->stream);
+        int rr_st = 0, orth_st = 0;
+        if (e == cudaSuccess) e = read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st);
+        if (e == cudaSuccess) e = iteration_body<float>(h, s, b, s->hasP32);
+        if (e != cudaSuccess) return fail(e);
+        s->hasP32 = true;
+        if (st) st->iters++;
+    }
+    std::vector<double> r2, t2;
+    int a1, a2;
+    e = read_progress<float>(h, s, r2, t2, &a1, &a2, st);   // collects the last SpMM time
+    if (e != cudaSuccess) return fail(e);
+    if (theta_out)
+        for (int j = 0; j < k && j < static_cast<int>(t2.size()); ++j) theta_out[j] = t2[j];
+    if (st) st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return LOBPCG_OK;
 }
 

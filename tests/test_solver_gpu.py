@@ -63,21 +63,23 @@ def test_solve_small_matches_oracle(precond):
     assert np.all(rho <= 1.05e-6), rho
 
 
-def test_small_workload_n20k():
+@pytest.mark.parametrize("precond", ["diag", "bjacobi"])
+def test_small_workload_n20k(precond):
     """The small workload (n = 20,000, ~100 stored entries per row, float64
-    values, k = 8, nev = 5, diagonal preconditioner, tol 1e-6)."""
+    values, k = 8, nev = 5, tol 1e-6), diagonal and block-Jacobi forms."""
     p = synth.WORKLOADS["small_n20k"]
     A64 = synth.tile_matrix(p["n"], p["nnz_per_row"], seed=p["seed"], fp32=False)
     A = f32_matrix(A64)                     # the matrix the GPU stores
-    X0, X, X64, ev, rs, st = run_gpu_solve(A64, p["k"], p["nev"], seed=p["seed"] + synth.X0_SEED_OFFSET)
+    X0, X, X64, ev, rs, st = run_gpu_solve(A64, p["k"], p["nev"], precond=precond,
+                                           seed=p["seed"] + synth.X0_SEED_OFFSET)
     assert st["converged"] == 1
-    ref = olb.lobpcg(A, X0.astype(np.float64), p["nev"], tol=1e-10, maxiter=2000, precond="diag")
+    ref = olb.lobpcg(A, X0.astype(np.float64), p["nev"], tol=1e-10, maxiter=2000, precond=precond)
     normG = oracle.gershgorin(A)
     assert np.all(eig_err(ev, ref.evals, normG) <= 1e-8)
     assert np.all(residuals_fp64(A, X64[:, :p["nev"]], ev) <= 1.05e-6)
     # against the float64 matrix: the float32 rounding of H moves eigenvalues
     # by at most ||dH||_2 <= eps32 ||H||_G (Weyl)
-    ref64 = olb.lobpcg(A64, X0.astype(np.float64), p["nev"], tol=1e-10, maxiter=2000, precond="diag")
+    ref64 = olb.lobpcg(A64, X0.astype(np.float64), p["nev"], tol=1e-10, maxiter=2000, precond=precond)
     assert np.all(np.abs(ev - ref64.evals) <= 6e-8 * normG + 1e-8 * np.abs(ref64.evals))
 
 
