@@ -1,0 +1,80 @@
+"""Pins for the oracle network of the learned preconditioner: central
+finite differences of the loss for every parameter block, a linear special
+case with a closed-form gradient, and Adam against its textbook update."""
+import numpy as np
+
+import synth
+from oracle import mlp
+
+
+def small_params(seed=0):
+    return mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, seed, 1), synth.normals(mlp.N_OUT * mlp.N_HID, seed, 2))
+
+
+def test_init_scale():
+    p = small_params()
+    assert p["W1"].shape == (256, 129) and p["W2"].shape == (64, 256)
+    assert abs(p["W1"].std() - np.sqrt(2 / 129)) < 0.01
+    assert not p["b1"].any() and not p["b2"].any()
+
+
+def test_gradients_finite_differences():
+    rng = np.random.default_rng(1)
+    p = small_params(3)
+    p["b1"] = rng.standard_normal(256) * 0.1
+    p["b2"] = rng.standard_normal(64) * 0.1
+    X = rng.standard_normal((7, 129))
+    T = rng.standard_normal((7, 64))
+    L, g = mlp.loss_and_grads(p, X, T)
+    h = 1e-6
+    for key in ("W1", "b1", "W2", "b2"):
+        flat = p[key].reshape(-1)
+        for idx in rng.choice(flat.size, size=12, replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = mlp.loss_and_grads(p, X, T)
+            flat[idx] = old - h
+            lm, _ = mlp.loss_and_grads(p, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[key].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-9, (key, idx, fd, an)
+
+
+def test_linear_case_closed_form():
+    """With all pre-activations positive the net is affine: Y = X A^T + c with
+    A = W2 W1, and dL/db2 = 2 (Y - T) summed / (B 64)."""
+    rng = np.random.default_rng(2)
+    p = small_params(5)
+    p["W1"] = np.abs(p["W1"])
+    p["b1"] = np.full(256, 10.0)
+    X = np.abs(rng.standard_normal((5, 129)))
+    T = rng.standard_normal((5, 64))
+    Y, _ = mlp.forward(p, X)
+    A = p["W2"] @ p["W1"]
+    c = p["W2"] @ p["b1"] + p["b2"]
+    assert np.allclose(Y, X @ A.T + c, rtol=1e-12, atol=1e-10)
+    _, g = mlp.loss_and_grads(p, X, T)
+    assert np.allclose(g["b2"], 2 * (Y - T).sum(0) / (5 * 64), rtol=1e-12)
+
+
+def test_adam_textbook():
+    p = {"a": np.array([1.0, -2.0])}
+    g = {"a": np.array([0.5, 0.25])}
+    m = {"a": np.zeros(2)}
+    v = {"a": np.zeros(2)}
+    p, m, v = mlp.adam_step(p, g, m, v, t=1, lr=0.1)
+    # first step of bias-corrected Adam moves each weight by lr * sign(g) (up to eps)
+    assert np.allclose(p["a"], [1.0 - 0.1, -2.0 - 0.1], atol=1e-6)
+
+
+def test_tile_inputs_and_target():
+    r = np.zeros(64)
+    r[3] = 3.0
+    r[5] = 4.0
+    d = np.linspace(1, 2, 64)
+    x, s = mlp.tile_inputs(r, d, 0.5, 10.0)
+    assert s == 5.0 and x.shape == (129,)
+    assert x[3] == 0.6 and x[5] == 0.8 and np.isclose(x[64], 0.05) and x[128] == 0.05
+    t = mlp.tile_target(np.full(64, 1e9), 1.0, 2.0)
+    assert np.all(t == mlp.CLIP)
