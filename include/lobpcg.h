@@ -177,7 +177,10 @@ LOBPCG_API lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double
  *   mode 1: 1x1 tiles, w_ij = r_ij / g(h_ii - theta_j)
  *   mode 2: 64-row tiles solved exactly through their eigendecompositions
  *           (needs params.precond == 2 at create, else ERR_UNSUPPORTED)
- *   mode 3: the learned tile network (after lobpcg_precond_train)
+ *   mode 3: the learned tile network (needs params.precond == 3 at create
+ *           and weights from lobpcg_precond_train or lobpcg_mlp_set_params);
+ *           k <= params.k.  A correction entry that is not finite is
+ *           dropped (that entry keeps its mode-1 value).
  *   R, W  : float32 n x k row-major, device (may be the same buffer)
  *   theta : float64[k], device
  */
@@ -229,6 +232,75 @@ LOBPCG_API lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t ste
 
 /* The last solve's Ritz vectors in float64 (n x k row-major, device or host). */
 LOBPCG_API lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X);
+
+/*
+ * Learned tile preconditioner (mode 3).  The paper has no counterpart: its K
+ * (Section 3.3) solves each shifted diagonal tile by a few FOM iterations;
+ * here one network, shared by every 64-row diagonal tile T, corrects the
+ * mode-1 (diagonal) solve.  It maps
+ *   x = [ r_T / s , (d_T - theta_j) / g , theta_j / g ]   (129 inputs)
+ * through h = relu(W1 x + b1) (256) to y = W2 h + b2 (64) and returns
+ * w_T = D^{-1} r_T + (s / g) y, D^{-1} r_T the mode-1 result, with
+ * s = ||r_T||_2 (a tile with s = 0 gives w_T = 0), d_T the tile's diagonal
+ * and g = ||H||_G (Gershgorin bound, lobpcg_info).
+ * A ragged last tile is zero-padded.  Products run on the tensor cores with
+ * bfloat16 operands (rounded from float32 master weights) and float32
+ * accumulation.  All entry points below need params.precond == 3 at create
+ * (ERR_UNSUPPORTED otherwise).
+ *
+ * Parameter vector (float32, LOBPCG_MLP_NPARAM entries, row-major blocks):
+ *   W1 [256][129] | b1 [256] | W2 [64][256] | b2 [64]
+ */
+#define LOBPCG_MLP_NPARAM 49728
+
+/* Load the weights (host or device pointer, `count` must equal
+ * LOBPCG_MLP_NPARAM); resets the Adam state.  Synchronises the stream. */
+LOBPCG_API lobpcg_status lobpcg_mlp_set_params(lobpcg_t h, const float *params, int64_t count);
+
+/* Copy out the weights (which = 0) or the gradients of the last
+ * lobpcg_mlp_grad / training batch (which = 1), same layout, host or device
+ * pointer.  Synchronises the stream. */
+LOBPCG_API lobpcg_status lobpcg_mlp_get_params(lobpcg_t h, float *out, int64_t count, int32_t which);
+
+/* Forward pass on B input rows: Xin float32 B x 129 row-major, Y float32
+ * B x 64 row-major, both device.  B >= 1.  Device scratch is taken from the
+ * stream-ordered pool and returned before the call ends. */
+LOBPCG_API lobpcg_status lobpcg_mlp_forward(lobpcg_t h, const float *Xin, int64_t B, float *Y);
+
+/* Mean squared error L = sum (Y - T)^2 / (64 B) of the forward pass on Xin
+ * against targets T (float32 B x 64, device), and its gradients with respect
+ * to every weight (kept on the handle; read them with lobpcg_mlp_get_params
+ * which = 1).  loss: host double (may be NULL).  Synchronises the stream. */
+LOBPCG_API lobpcg_status lobpcg_mlp_grad(lobpcg_t h, const float *Xin, const float *T, int64_t B, double *loss);
+
+/* One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected by the handle's step count) of the weights along the held
+ * gradients, learning rate lr > 0. */
+LOBPCG_API lobpcg_status lobpcg_mlp_adam(lobpcg_t h, float lr);
+
+/*
+ * Train the network on pairs the solver itself produces.  (1) Run
+ * harvest_iters float32 LOBPCG iterations from X0 with the exact block-Jacobi
+ * tile solves; in each, every (tile, column) pair is kept with probability
+ * about n_pairs / (harvest_iters * tiles * k) (seeded by params.seed) and
+ * stored as (x, t = clip(g (y_T - D^{-1} r_T) / s, +-1e3)), y_T the exact
+ * shifted solve.  (2) If no weights were set, draw initial weights from
+ * params.seed: W1 He-normal, b1, W2 and b2 zero (so that the untrained form
+ * is the diagonal one).  (3) The last tenth of the pairs is held out; the
+ * rest is visited `epochs` times with mean-squared-error Adam steps
+ * (learning rate lr) over batches of up to 4096 pairs in a permuted order,
+ * and the weights with the lowest held-out loss (before training or after an
+ * epoch) are kept.
+ *   X0        : float32 n x k (device or host), the solve's initial guess
+ *   n_pairs   : capacity of the pair buffer (>= 4096); 772 bytes each
+ *   loss_hist : host double[epochs + 1], held-out mean squared error before
+ *               training and after each epoch (may be NULL)
+ *   pairs_used: host (may be NULL), pairs actually harvested (<= n_pairs)
+ * The pair buffer is freed before return.  Returns ERR_ARG when fewer than
+ * 4096 pairs were harvested.  Synchronises the stream.
+ */
+LOBPCG_API lobpcg_status lobpcg_precond_train(lobpcg_t h, int32_t harvest_iters, int64_t n_pairs, int32_t epochs,
+                                              const float *X0, float lr, double *loss_hist, int64_t *pairs_used);
 
 #ifdef __cplusplus
 }

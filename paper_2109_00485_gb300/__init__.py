@@ -23,6 +23,7 @@ STATUS = {
     6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_BOUNDS", 9: "ERR_UNSUPPORTED",
 }
 MEM_DEVICE, MEM_HOST = 0, 1
+MLP_NPARAM = 49728      # W1 [256][129] | b1 [256] | W2 [64][256] | b2 [64]
 PRECOND = {"none": 0, "diag": 1, "bjacobi": 2, "mlp": 3}
 
 
@@ -96,6 +97,19 @@ def load():
     L.lobpcg_iterate.restype = st
     L.lobpcg_get_x_f64.argtypes = [vp, vp]
     L.lobpcg_get_x_f64.restype = st
+    i64 = ctypes.c_int64
+    L.lobpcg_mlp_set_params.argtypes = [vp, vp, i64]
+    L.lobpcg_mlp_set_params.restype = st
+    L.lobpcg_mlp_get_params.argtypes = [vp, vp, i64, i32]
+    L.lobpcg_mlp_get_params.restype = st
+    L.lobpcg_mlp_forward.argtypes = [vp, vp, i64, vp]
+    L.lobpcg_mlp_forward.restype = st
+    L.lobpcg_mlp_grad.argtypes = [vp, vp, vp, i64, vp]
+    L.lobpcg_mlp_grad.restype = st
+    L.lobpcg_mlp_adam.argtypes = [vp, ctypes.c_float]
+    L.lobpcg_mlp_adam.restype = st
+    L.lobpcg_precond_train.argtypes = [vp, i32, i64, i32, vp, ctypes.c_float, vp, vp]
+    L.lobpcg_precond_train.restype = st
     _lib = L
     return L
 
@@ -237,6 +251,58 @@ class Handle:
     def lobpcg_sync(self):
         _check(self._h, load().lobpcg_sync(self._h))
 
+    # -- learned tile preconditioner (mode 3) --------------------------------
+    def lobpcg_mlp_set_params(self, params):
+        """Load weights: float32 vector of MLP_NPARAM (numpy or CUDA tensor)."""
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self._h, load().lobpcg_mlp_set_params(self._h, _ptr(params), int(params.size if isinstance(
+            params, np.ndarray) else params.numel())))
+
+    def lobpcg_mlp_get_params(self, which: str = "weights") -> np.ndarray:
+        """Weights (or 'grads', the gradients of the last batch) as float32 numpy."""
+        out = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(self._h, load().lobpcg_mlp_get_params(self._h, out.ctypes.data, MLP_NPARAM,
+                                                     {"weights": 0, "grads": 1}[which]))
+        return out
+
+    def lobpcg_mlp_forward(self, Xin, Y=None):
+        """Y (B x 64) = network(Xin (B x 129)), float32 CUDA tensors."""
+        import torch
+        B = Xin.shape[0]
+        if tuple(Xin.shape) != (B, 129) or Xin.dtype != torch.float32 or not Xin.is_cuda or not Xin.is_contiguous():
+            raise ValueError("Xin must be a contiguous CUDA float32 (B, 129) tensor")
+        if Y is None:
+            Y = torch.empty((B, 64), dtype=torch.float32, device=Xin.device)
+        _check(self._h, load().lobpcg_mlp_forward(self._h, _ptr(Xin), B, _ptr(Y)))
+        return Y
+
+    def lobpcg_mlp_grad(self, Xin, T) -> float:
+        """Batch MSE loss of Xin (B x 129) against T (B x 64); gradients kept
+        on the handle (``mlp_get_params('grads')``)."""
+        B = Xin.shape[0]
+        if tuple(T.shape) != (B, 64) or tuple(Xin.shape) != (B, 129):
+            raise ValueError("Xin must be (B, 129) and T (B, 64)")
+        loss = ctypes.c_double(0.0)
+        _check(self._h, load().lobpcg_mlp_grad(self._h, _ptr(Xin), _ptr(T), B, ctypes.addressof(loss)))
+        return loss.value
+
+    def lobpcg_mlp_adam(self, lr: float = 1e-3):
+        _check(self._h, load().lobpcg_mlp_adam(self._h, float(lr)))
+
+    def lobpcg_precond_train(self, X0, harvest_iters: int = 20, n_pairs: int = 1 << 20, epochs: int = 5,
+                             lr: float = 1e-3):
+        """Harvest (residual, exact tile solve) pairs from block-Jacobi
+        iterations from X0, then train the network.  Returns (held-out loss
+        before training and after each epoch, pairs used)."""
+        if isinstance(X0, np.ndarray):
+            X0 = np.ascontiguousarray(X0, dtype=np.float32)
+        hist = np.zeros(epochs + 1)
+        used = ctypes.c_int64(0)
+        _check(self._h, load().lobpcg_precond_train(self._h, int(harvest_iters), int(n_pairs), int(epochs),
+                                                    _ptr(X0), float(lr), hist.ctypes.data, ctypes.addressof(used)))
+        return hist, used.value
+
     def lobpcg_matrix_info(self) -> dict:
         info = _Info()
         _check(self._h, load().lobpcg_matrix_info(self._h, ctypes.byref(info)))
@@ -260,6 +326,12 @@ class Handle:
     iterate = lobpcg_iterate
     get_x_f64 = lobpcg_get_x_f64
     sync = lobpcg_sync
+    mlp_set_params = lobpcg_mlp_set_params
+    mlp_get_params = lobpcg_mlp_get_params
+    mlp_forward = lobpcg_mlp_forward
+    mlp_grad = lobpcg_mlp_grad
+    mlp_adam = lobpcg_mlp_adam
+    precond_train = lobpcg_precond_train
     info = lobpcg_matrix_info
     destroy = lobpcg_destroy
 

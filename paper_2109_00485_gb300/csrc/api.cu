@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "lobpcg.h"
 #include "precond.h"
+#include "mlp.h"
 
 using namespace lobpcg;
 
@@ -31,6 +32,7 @@ void release(lobpcg_ctx *h) {
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     solver_release(h);
+    mlp_release(h);
     if (h->stage_x) cudaFree(h->stage_x);
     if (h->stage_y) cudaFree(h->stage_y);
     h->stage_x = h->stage_y = nullptr;
@@ -131,7 +133,9 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     std::string err;
     lobpcg_status st = LOBPCG_ERR_CUDA;
     e = build_tiled(h, rp, cl, vl, A->val_is_fp64 != 0, err, st);
-    if (e == cudaSuccess && st == LOBPCG_OK && P.precond == 2) e = bjacobi_setup(h, rp, cl, vl, A->val_is_fp64 != 0);
+    if (e == cudaSuccess && st == LOBPCG_OK && (P.precond == 2 || P.precond == 3))
+        e = bjacobi_setup(h, rp, cl, vl, A->val_is_fp64 != 0);   // the learned form trains on exact tile solves
+    if (e == cudaSuccess && st == LOBPCG_OK && P.precond == 3) e = mlp_setup(h);
     if (e == cudaSuccess && st == LOBPCG_OK) e = solver_setup(h);
     if (e == cudaSuccess && st == LOBPCG_OK) e = cudaStreamSynchronize(h->stream);
     if (tmp) {
@@ -236,7 +240,9 @@ lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *the
     if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     if (mode < 0 || mode > 3) return fail(h, LOBPCG_ERR_ARG, "mode must be 0..3");
     if (mode == 2 && !h->bj_Q) return fail(h, LOBPCG_ERR_UNSUPPORTED, "block-Jacobi needs params.precond = 2 at create");
-    if (mode == 3) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner not trained");
+    if (mode == 3 && !h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (mode == 3 && !h->mlp.ready) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner has no weights");
+    if (mode == 3 && k > h->params.k) return fail(h, LOBPCG_ERR_ARG, "learned form: k must be <= params.k");
     cudaError_t e = precond_apply<float>(h, mode, k, R, theta, W, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "precond_apply");
     return LOBPCG_OK;
@@ -272,6 +278,8 @@ lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, l
     if (!h) return LOBPCG_ERR_ARG;
     if (!X) return fail(h, LOBPCG_ERR_ARG, "X is NULL");
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
+    if (h->params.precond == 3 && !h->mlp.ready)
+        return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner has no weights (train or set them first)");
     std::string err;
     lobpcg_status s = solve(h, X, is_host_ptr(X), evals, resid, st, err);
     if (s != LOBPCG_OK) return fail(h, s, err);
@@ -282,6 +290,8 @@ lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double 
     if (!h) return LOBPCG_ERR_ARG;
     if (steps < 0) return fail(h, LOBPCG_ERR_ARG, "steps must be >= 0");
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
+    if (h->params.precond == 3 && !h->mlp.ready)
+        return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner has no weights (train or set them first)");
     std::string err;
     lobpcg_status s = iterate(h, X0, X0 ? is_host_ptr(X0) : false, steps, theta, st, err);
     if (s != LOBPCG_OK) return fail(h, s, err);
@@ -292,6 +302,82 @@ lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X) {
     if (!h || !X) return LOBPCG_ERR_ARG;
     cudaError_t e = copy_x_f64(h, X);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_x_f64");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_mlp_set_params(lobpcg_t h, const float *params, int64_t count) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!params || count != MLP_NPARAM_CALLER) return fail(h, LOBPCG_ERR_ARG, "params NULL or count != 49728");
+    cudaError_t e = mlp_set_params(h, params, is_host_ptr(params));
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp_set_params");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_mlp_get_params(lobpcg_t h, float *out, int64_t count, int32_t which) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!out || count != MLP_NPARAM_CALLER) return fail(h, LOBPCG_ERR_ARG, "out NULL or count != 49728");
+    if (which != 0 && which != 1) return fail(h, LOBPCG_ERR_ARG, "which must be 0 (weights) or 1 (gradients)");
+    cudaError_t e = mlp_get_params(h, out, is_host_ptr(out), which == 1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp_get_params");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_mlp_forward(lobpcg_t h, const float *Xin, int64_t B, float *Y) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!Xin || !Y || B < 1 || B > (int64_t(1) << 30)) return fail(h, LOBPCG_ERR_ARG, "Xin/Y NULL or B out of range");
+    cudaError_t e = mlp_forward_rows(h, Xin, B, Y);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp_forward");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_mlp_grad(lobpcg_t h, const float *Xin, const float *T, int64_t B, double *loss) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!Xin || !T || B < 1 || B > (int64_t(1) << 30)) return fail(h, LOBPCG_ERR_ARG, "Xin/T NULL or B out of range");
+    double l = 0.0;
+    cudaError_t e = mlp_grad_rows(h, Xin, T, B, &l);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp_grad");
+    if (loss) *loss = l;
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_mlp_adam(lobpcg_t h, float lr) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!(lr > 0.f)) return fail(h, LOBPCG_ERR_ARG, "lr must be > 0");
+    cudaError_t e = mlp_adam(h, lr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mlp_adam");
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_precond_train(lobpcg_t h, int32_t harvest_iters, int64_t n_pairs, int32_t epochs,
+                                   const float *X0, float lr, double *loss_hist, int64_t *pairs_used) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
+    if (!X0) return fail(h, LOBPCG_ERR_ARG, "X0 is NULL");
+    if (harvest_iters < 1 || epochs < 0 || n_pairs < MLP_BATCH || n_pairs > (int64_t(1) << 32) || !(lr > 0.f))
+        return fail(h, LOBPCG_ERR_ARG, "need harvest_iters >= 1, epochs >= 0, 4096 <= n_pairs <= 2^32, lr > 0");
+    cudaError_t e = mlp_alloc_pairs(h, n_pairs, harvest_iters);
+    if (e != cudaSuccess) {
+        mlp_release(h);
+        return cuda_fail(h, e, "pair buffer");
+    }
+    std::string err;
+    lobpcg_status s = iterate(h, X0, is_host_ptr(X0), harvest_iters, nullptr, nullptr, err, 1);
+    if (s != LOBPCG_OK) {
+        mlp_release(h);
+        return fail(h, s, "harvest: " + err);
+    }
+    if (!h->mlp.ready) e = mlp_init(h, h->params.seed);
+    int64_t np = 0;
+    if (e == cudaSuccess) e = mlp_train(h, epochs, lr, loss_hist, &np);
+    mlp_release(h);
+    if (pairs_used) *pairs_used = np;
+    if (e == cudaErrorInvalidValue) return fail(h, LOBPCG_ERR_ARG, "fewer than 4096 pairs harvested");
+    if (e != cudaSuccess) return cuda_fail(h, e, "precond_train");
     return LOBPCG_OK;
 }
 

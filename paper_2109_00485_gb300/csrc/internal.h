@@ -5,6 +5,7 @@
 #include <vector>
 #include <cuda_runtime.h>
 #include "lobpcg.h"
+#include "mlp.h"
 
 namespace lobpcg {
 
@@ -65,6 +66,7 @@ struct lobpcg_ctx {
     float *bj_Q = nullptr;       // block-Jacobi: per 64-row tile eigenvectors (64 x 64) and eigenvalues
     float *bj_lam = nullptr;
     lobpcg::SolverState *solver = nullptr;  // workspaces of lobpcg_solve (solver.cu)
+    lobpcg::Mlp mlp;                         // learned tile preconditioner (mlp.cu)
     std::string last_error;
 };
 
@@ -88,6 +90,6 @@ lobpcg_status solve(lobpcg_ctx *h, float *X, bool x_on_host, double *evals, doub
                     std::string &err);
 cudaError_t copy_x_f64(lobpcg_ctx *h, double *out);
 lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps, double *theta_out,
-                      lobpcg_stats *st, std::string &err);
+                      lobpcg_stats *st, std::string &err, int harvest = 0);
 
 }  // namespace lobpcg

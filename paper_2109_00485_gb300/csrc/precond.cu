@@ -7,10 +7,12 @@
 //                 decomposition H_T = Q diag(lam) Q^T (computed once, FP64
 //                 Jacobi, stored FP32): w_T = Q diag(1/g(lam - theta_j)) Q^T r_T
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "internal.h"
 #include "precond.h"
+#include "mlp.h"
 
 namespace lobpcg {
 
@@ -206,6 +208,12 @@ cudaError_t precond_apply(const lobpcg_ctx *h, int mode, int k, const T *R, cons
         if (e != cudaSuccess) return e;
         k_bjacobi_apply<T><<<static_cast<unsigned>(nt), 256, smem, s>>>(n, k, h->bj_Q, h->bj_lam, R, theta, W);
         return cudaGetLastError();
+    }
+    if (mode == 3) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!h->mlp.ready) return cudaErrorInvalidValue;
+            return mlp_apply(const_cast<lobpcg_ctx *>(h), k, R, theta, W, s);
+        }
     }
     return cudaErrorInvalidValue;
 }

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 #include <cuda_runtime.h>
 #include "common.cuh"
@@ -27,6 +28,7 @@
 #include "internal.h"
 #include "lobpcg.h"
 #include "precond.h"
+#include "mlp.h"
 
 namespace lobpcg {
 
@@ -200,13 +202,33 @@ cudaError_t rr_on_x(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
 
 // Everything of one iteration after the residual (W = K^{-1} R in b.W):
 // preconditioner, orthonormalisation, H W, Gram, Rayleigh-Ritz, update.
+// Preconditioner used by a phase: the float64 refinement applies the
+// diagonal form in place of the learned one.
 template <typename T>
-cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
+int effective_precond(const lobpcg_ctx *h) {
+    const int p = h->params.precond;
+    return (std::is_same<T, double>::value && p == 3) ? 1 : p;
+}
+
+template <typename T>
+cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP, int pmode, int harvest_iter = -1) {
     const int k = s->k;
     const int64_t n = h->T.n;
-    const int pmode = h->params.precond;
         // preconditioner (the diagonal one was applied inside the residual kernel)
-        if (pmode == 2) CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
+        if (pmode == 2) {
+            if constexpr (std::is_same<T, float>::value) {
+                if (harvest_iter >= 0) {   // exact tile solves into HW, harvest (R, solve) pairs, then W = HW
+                    CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.HW, h->stream));
+                    CK(mlp_harvest(h, k, b.W, b.HW, s->theta, harvest_iter));
+                    CK(cudaMemcpyAsync(b.W, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
+                } else {
+                    CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
+                }
+            } else {
+                CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
+            }
+        }
+        if (pmode == 3) CK(precond_apply<T>(h, 3, k, b.W, s->theta, b.W, h->stream));
         // orthonormalise W against X and itself
         CK(orth_pass<T>(h, s, b));
         CK(orth_pass<T>(h, s, b));
@@ -249,7 +271,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
     const int64_t n = h->T.n;
     const double tol = h->params.tol;
     Blocks<T> &b = blocks_of<T>(s);
-    const int pmode = h->params.precond;
+    const int pmode = effective_precond<T>(h);
     status = LOBPCG_OK;
 
     CK(spmm_T<T>(h, b.X, b.HX, k));
@@ -305,7 +327,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
         }
         if (res.iters >= max_iters) break;
         ++res.iters;
-        CK(iteration_body<T>(h, s, b, hasP));
+        CK(iteration_body<T>(h, s, b, hasP, pmode));
         hasP = true;
     }
     res.rho = rho;
@@ -429,7 +451,7 @@ lobpcg_status solve(lobpcg_ctx *h, float *Xio, bool x_on_host, double *evals, do
 // norms are still formed and read each iteration, as in the solve).  X0 (n x k,
 // device or host) starts a new run; NULL continues the previous one.
 lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps, double *theta_out,
-                      lobpcg_stats *st, std::string &err) {
+                      lobpcg_stats *st, std::string &err, int harvest) {
     SolverState *s = h->solver;
     const int k = s->k;
     const int64_t n = h->T.n;
@@ -455,13 +477,13 @@ lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps,
         return LOBPCG_ERR_ARG;
     }
     std::vector<double> rho, theta;
-    const int pmode = h->params.precond;
+    const int pmode = harvest ? 2 : h->params.precond;   // harvesting runs the exact tile solves
     for (int it = 0; it < steps; ++it) {
         e = launch_resid<float>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
                                 h->stream);
         int rr_st = 0, orth_st = 0;
         if (e == cudaSuccess) e = read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st);
-        if (e == cudaSuccess) e = iteration_body<float>(h, s, b, s->hasP32);
+        if (e == cudaSuccess) e = iteration_body<float>(h, s, b, s->hasP32, pmode, harvest ? it : -1);
         if (e != cudaSuccess) return fail(e);
         s->hasP32 = true;
         if (st) st->iters++;
