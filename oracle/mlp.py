@@ -5,33 +5,38 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 The paper's preconditioner K (Section 3.3) solves each shifted diagonal tile
 (H_T - theta I) w_T = r_T (by 3-5 FOM iterations).  The learned form replaces
 that solve by one small network shared by every 64-row tile (not in the
-paper; its readings are listed in the design notes):
+paper; its readings are listed in the design notes).  The network supplies a
+correction to the diagonal (1x1-tile) solve D_theta^{-1} r_T:
 
   input  x = [ r_T / s , (d_T - theta) / g , theta / g ]   (64 + 64 + 1 = 129)
            s = ||r_T||_2,  g = ||H||_G,  d_T = diag of the tile
   hidden h = relu(W1 x + b1)                                (256)
   output y = W2 h + b2                                      (64)
-  w_T   = (s / g) y
+  w_T   = D_theta^{-1} r_T + (s / g) y
 
-trained on target t = clip(g y_T / s, -1e3, 1e3) where y_T is the exact tile
-solve, by mean squared error over the 64 outputs and the batch, with Adam
-(beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Parameters are a dict
-of W1 (256 x 129), b1 (256), W2 (64 x 256), b2 (64).
+with D_theta^{-1} the guarded diagonal solve of oracle.precond.apply_diag.
+It is trained on the target t = clip(g (y_T - D_theta^{-1} r_T) / s, +-1e3),
+y_T the exact tile solve, by mean squared error over the 64 outputs and the
+batch, with Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  The
+output layer starts at zero, so the untrained form is the diagonal one.
+Parameters are a dict of W1 (256 x 129), b1 (256), W2 (64 x 256), b2 (64).
 """
 from __future__ import annotations
 
 import numpy as np
+
+from .precond import apply_diag
 
 N_IN, N_HID, N_OUT = 129, 256, 64
 TILE = 64
 CLIP = 1e3
 
 
-def init_params(normals_w1: np.ndarray, normals_w2: np.ndarray) -> dict:
-    """He (Kaiming) normal init from given N(0,1) draws: W ~ N(0, 2 / fan_in),
-    biases zero."""
+def init_params(normals_w1: np.ndarray) -> dict:
+    """Initial weights: W1 He (Kaiming) normal from given N(0,1) draws,
+    W1 ~ N(0, 2 / 129); b1, W2 and b2 zero."""
     return {"W1": normals_w1.reshape(N_HID, N_IN) * np.sqrt(2.0 / N_IN), "b1": np.zeros(N_HID),
-            "W2": normals_w2.reshape(N_OUT, N_HID) * np.sqrt(2.0 / N_HID), "b2": np.zeros(N_OUT)}
+            "W2": np.zeros((N_OUT, N_HID)), "b2": np.zeros(N_OUT)}
 
 
 def forward(p: dict, X: np.ndarray):
@@ -74,16 +79,22 @@ def tile_inputs(r: np.ndarray, d: np.ndarray, theta: float, normG: float):
     return x, s
 
 
-def tile_target(y: np.ndarray, s: float, normG: float) -> np.ndarray:
-    return np.clip(normG * y / s, -CLIP, CLIP)
+def tile_target(y: np.ndarray, r: np.ndarray, d: np.ndarray, theta: float, normG: float) -> np.ndarray:
+    """Training target of one tile column: exact solve y, residual r, tile
+    diagonal d (all length 64)."""
+    s = float(np.linalg.norm(r))
+    yd = apply_diag(d, r[:, None], np.array([theta]))[:, 0]
+    return np.clip(normG * (y - yd) / s, -CLIP, CLIP)
 
 
 def apply(p: dict, R: np.ndarray, d: np.ndarray, theta: np.ndarray, normG: float) -> np.ndarray:
-    """w_T = (s / g) MLP(x) for every 64-row tile and column (a ragged last
-    tile is zero-padded; tiles with s = 0 give w_T = 0).  Parity unpinned
-    beyond its pieces (forward pinned through the gradient checks)."""
+    """w_T = D_theta^{-1} r_T + (s / g) MLP(x) for every 64-row tile and column
+    (a ragged last tile is zero-padded; tiles with s = 0 give w_T = 0).
+    Pinned through its pieces: the forward pass by the gradient checks, the
+    diagonal part by apply_diag's own pins, and a zero output layer giving
+    exactly the diagonal solve."""
     n, k = R.shape
-    W = np.zeros_like(R)
+    W = apply_diag(d, R, theta)
     for t0 in range(0, n, TILE):
         m = min(TILE, n - t0)
         for j in range(k):
@@ -95,5 +106,5 @@ def apply(p: dict, R: np.ndarray, d: np.ndarray, theta: np.ndarray, normG: float
             if s == 0.0:
                 continue
             y, _ = forward(p, x[None, :])
-            W[t0:t0 + m, j] = (s / normG) * y[0, :m]
+            W[t0:t0 + m, j] += (s / normG) * y[0, :m]
     return W

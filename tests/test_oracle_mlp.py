@@ -8,14 +8,18 @@ from oracle import mlp
 
 
 def small_params(seed=0):
-    return mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, seed, 1), synth.normals(mlp.N_OUT * mlp.N_HID, seed, 2))
+    """Initial weights with a random output layer (the initial one is zero),
+    so that every gradient block is exercised."""
+    p = mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, seed, 1))
+    p["W2"] = synth.normals(mlp.N_OUT * mlp.N_HID, seed, 2).reshape(64, 256) * np.sqrt(2 / 256)
+    return p
 
 
 def test_init_scale():
-    p = small_params()
+    p = mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, 0, 1))
     assert p["W1"].shape == (256, 129) and p["W2"].shape == (64, 256)
     assert abs(p["W1"].std() - np.sqrt(2 / 129)) < 0.01
-    assert not p["b1"].any() and not p["b2"].any()
+    assert not p["b1"].any() and not p["W2"].any() and not p["b2"].any()
 
 
 def test_gradients_finite_differences():
@@ -76,5 +80,26 @@ def test_tile_inputs_and_target():
     x, s = mlp.tile_inputs(r, d, 0.5, 10.0)
     assert s == 5.0 and x.shape == (129,)
     assert x[3] == 0.6 and x[5] == 0.8 and np.isclose(x[64], 0.05) and x[128] == 0.05
-    t = mlp.tile_target(np.full(64, 1e9), 1.0, 2.0)
-    assert np.all(t == mlp.CLIP)
+    # target = g (y - r / (d - theta)) / s, clipped
+    r = np.ones(64)
+    d = np.full(64, 3.0)
+    t = mlp.tile_target(np.full(64, 0.75), r, d, 1.0, 4.0)
+    assert np.allclose(t, 4.0 * (0.75 - 0.5) / 8.0)
+    assert np.all(mlp.tile_target(np.full(64, 1e9), r, d, 1.0, 2.0) == mlp.CLIP)
+
+
+def test_untrained_apply_is_the_diagonal_solve():
+    """A zero output layer leaves exactly the 1x1-tile solve r_i / (d_i - theta_j)
+    (pivots kept away from the guard), including a ragged last tile; a random
+    output layer changes every tile."""
+    rng = np.random.default_rng(4)
+    n, k = 150, 3
+    R = rng.standard_normal((n, k))
+    d = rng.uniform(3, 10, n)
+    theta = np.array([-1.0, 0.3, 2.0])
+    p = mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, 1, 1))
+    W = mlp.apply(p, R, d, theta, 12.0)
+    assert np.array_equal(W, R / (d[:, None] - theta[None, :]))
+    W2 = mlp.apply(small_params(2), R, d, theta, 12.0)
+    for t0 in (0, 64, 128):
+        assert not np.allclose(W2[t0:t0 + 64], W[t0:t0 + 64])
