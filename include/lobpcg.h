@@ -202,6 +202,27 @@ LOBPCG_API lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const 
                                               double *C, double *theta);
 
 /*
+ * lobpcg_rayleigh_ritz with no allocation.  The paper has no counterpart: it
+ * is the same computation as lobpcg_rayleigh_ritz (same arguments, results
+ * and errors) for callers that must not let a library call allocate (a loop
+ * that reserved all device memory up front, a hard memory budget, or a loop
+ * where an allocator call could block on other device work).  Its G and O
+ * workspaces live in one statically sized device array of the library
+ * (147,472 bytes per device: m <= 96; a larger m gives ERR_ARG with the
+ * sizes in lobpcg_last_error).  The call clears G and O itself; nothing has
+ * to be zero beforehand.
+ *   - The array's device address is looked up once per device, on that
+ *     device's first call; make that first call before any stream capture
+ *     and with the handle's device current.
+ *   - The array is shared by all calls on a device: calls that overlap in
+ *     time (other streams, threads or handles) race on it and their results
+ *     are undefined.  After return it keeps the last call's contents.
+ *   - Synchronises the handle's stream (to read the breakdown status).
+ */
+LOBPCG_API lobpcg_status lobpcg_rayleigh_ritz_noalloc(lobpcg_t h, const float *S, const float *HS, int32_t m,
+                                                      int32_t k, double *C, double *theta);
+
+/*
  * The k leftmost eigenpairs of H by block LOBPCG (Algorithm 1), with the
  * preconditioner, tolerance and limits of the create parameters.  Only one
  * SpMM (H W) per iteration: HX and HP follow the recurrences of eqs.

@@ -91,6 +91,8 @@ def load():
     L.lobpcg_precond_apply.restype = st
     L.lobpcg_rayleigh_ritz.argtypes = [vp, vp, vp, i32, i32, vp, vp]
     L.lobpcg_rayleigh_ritz.restype = st
+    L.lobpcg_rayleigh_ritz_noalloc.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    L.lobpcg_rayleigh_ritz_noalloc.restype = st
     L.lobpcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Stats)]
     L.lobpcg_solve.restype = st
     L.lobpcg_iterate.argtypes = [vp, vp, i32, vp, ctypes.POINTER(_Stats)]
@@ -205,6 +207,19 @@ class Handle:
         th = torch.empty((k,), dtype=torch.float64, device=S.device)
         _check(self._h, load().lobpcg_rayleigh_ritz(self._h, _ptr(S), _ptr(HS), m, k, _ptr(C), _ptr(th)))
         return C, th
+
+    def lobpcg_rayleigh_ritz_noalloc(self, S, HS, k: int, C, theta):
+        """``lobpcg_rayleigh_ritz`` into caller-provided C (float64 device
+        m x k) and theta (float64 device k); the library allocates nothing."""
+        import torch
+        m = S.shape[1]
+        _dev_block(S, "f32", self.n, m)
+        _dev_block(HS, "f32", self.n, m)
+        for t, shape in ((C, (m, k)), (theta, (k,))):
+            if not (t.is_cuda and t.dtype == torch.float64 and tuple(t.shape) == shape and t.is_contiguous()):
+                raise ValueError(f"expected a contiguous CUDA float64 tensor of shape {shape}")
+        _check(self._h, load().lobpcg_rayleigh_ritz_noalloc(self._h, _ptr(S), _ptr(HS), m, k, _ptr(C), _ptr(theta)))
+        return C, theta
 
     def lobpcg_solve(self, X0):
         """Run LOBPCG from X0 (float32 n x k: CUDA tensor, or host numpy / CPU
@@ -322,6 +337,7 @@ class Handle:
     spmm_sym_f64 = lobpcg_spmm_sym_f64
     precond_apply = lobpcg_precond_apply
     rayleigh_ritz = lobpcg_rayleigh_ritz
+    rayleigh_ritz_noalloc = lobpcg_rayleigh_ritz_noalloc
     solve = lobpcg_solve
     iterate = lobpcg_iterate
     get_x_f64 = lobpcg_get_x_f64
