@@ -123,6 +123,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Kernel launches of one LOBPCG iteration with a P block (from the ncu launch
+# list of this bench: resid, 2 x (4 Gram-type, projection, Cholesky-QR
+# factor, 2 combine, 2 coefficient casts), SpMM, Gram, P scaling,
+# Rayleigh-Ritz, 2 x (cast, combine) = 25).
+LAUNCHES_PER_ITERATION = 25
+
+
+def aggregate(total_ms: float, bytes_per_step: int, steps: int, world: int, device=None):
+    """Max of the timed region over ranks and the whole-job value (GB/s):
+    every rank runs its own replica, so the job moves world x bytes_per_step
+    per step in the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, bytes_per_step * steps * world / (total_ms / 1e3) / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -187,10 +207,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi")):
+def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "mlp")):
     """Time-to-solution (relative residual 1e-6, nev pairs) from a host X0,
     through lobpcg_solve; create (matrix tiling, preconditioner set-up) is
-    timed separately."""
+    timed separately.  The learned form ("mlp") is first trained on pairs
+    harvested from 20 block-Jacobi iterations from the same X0 (about 1M
+    pairs, 5 epochs, Adam lr 1e-3): its training time is reported on its own
+    and added in."""
     import torch
     out = {}
     X0 = synth.initial_guess(A, p["k"], seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
@@ -198,9 +221,15 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc, polish_fp64=1,
-                         stream=stream)
+                         stream=stream, seed=p["seed"])
         torch.cuda.synchronize()
         t_create = time.perf_counter() - t0
+        train = None
+        if pc == "mlp":
+            t0 = time.perf_counter()
+            hist, used = h.precond_train(X0, harvest_iters=20, n_pairs=1 << 20, epochs=5, lr=1e-3)
+            train = {"train_s": round(time.perf_counter() - t0, 3), "pairs": int(used),
+                     "held_out_mse": [round(float(v), 5) for v in hist]}
         t0 = time.perf_counter()
         try:
             X, ev, rs, st = h.solve(X0)
@@ -213,6 +242,9 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi")):
         out[pc] = {"time_to_solution_s": round(t_solve, 3), "create_s": round(t_create, 3),
                    "iters": st["iters"], "iters_fp64": st["iters_fp64"], "converged": bool(ok and st["converged"]),
                    "max_resid": float(np.max(rs)), "evals": [float(v) for v in ev]}
+        if train:
+            out[pc]["training"] = train
+            out[pc]["time_to_solution_with_training_s"] = round(t_solve + train["train_s"], 3)
     return out
 
 
@@ -275,14 +307,8 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = aggregate(e0.elapsed_time(e1), B, args.steps, world, dev)
     ms_step = total_ms / args.steps
-    value = B * args.steps * world / (total_ms / 1e3) / 1e9
     spmm_ms = st["spmm_ms"] / max(1, st["spmm_calls"])
 
     # e2e: the same metric through lobpcg_spmm_sym with pinned HOST X and Y
@@ -330,7 +356,7 @@ def main():
                            "l2": "inputs (6.4 GB matrix stream) larger than L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 20 * args.steps,
+                "gpu_launches": LAUNCHES_PER_ITERATION * args.steps,
                 "gflops_spmm": round(4.0 * k * nnz / (spmm_ms / 1e3) / 1e9, 1),
                 "lobpcg": solves,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],

@@ -108,7 +108,7 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the handle */
     double gershgorin;       /* ||H||_G = max_i sum_j |h_ij| over full rows */
     int32_t num_sms;
-    int32_t warps;           /* warps the SpMM partition is cut for */
+    int32_t warps;           /* warps the tiled SpMM kernel launches */
 } lobpcg_info;
 
 /*

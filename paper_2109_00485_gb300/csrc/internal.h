@@ -36,14 +36,13 @@ constexpr int NPAD_SHIFT = 20;
 //   chunk[c].ct    column tile of chunk c (col >> 4)
 //   chunk[c].info  real entry count | DIAG_FLAG (diagonal chunk) | npad << 20
 //   rb_chunk[rb]   first chunk of row block rb (rb_chunk[R] = nchunks)
-//   warp_rb[w]     first row block of SpMM warp w (warp_rb[W] = R)
 struct Tiled {
     int64_t n = 0, nnz = 0, R = 0, nchunks = 0, npad = 0, full_chunks = 0;
     uint32_t *data = nullptr;
     struct ChunkRec *chunk = nullptr;
     int64_t *rb_chunk = nullptr;
-    int32_t *warp_rb = nullptr;
-    int32_t warps = 0;
+    int32_t warps = 0;        // SpMM warps launched
+    int *sched = nullptr;     // SpMM work counter (row-block groups handed out)
     float *diag = nullptr;   // d_i = h_ii (float32)
 };
 

@@ -47,7 +47,8 @@ struct SpmmCfg {
     static constexpr int K = 8 * NT;
     static constexpr int STAGES = SPMM_STAGES;
     static constexpr int WARPS = SPMM_WARPS;
-    static constexpr int MINB = SPMM_MINB;
+    // two blocks fit in shared memory only up to k = 16
+    static constexpr int MINB = NT <= 2 ? SPMM_MINB : 1;
 };
 
 template <int NT>
@@ -60,14 +61,22 @@ struct __align__(16) WarpSmem {
     uint64_t bar[SpmmCfg<NT>::STAGES];
 };
 
+// Row blocks are handed out in order, SPMM_GROUP at a time, from a counter
+// in device memory (zeroed before each launch): all warps then work on a
+// narrow band of rows at any moment, so the X rows the band's tiles read and
+// the Y rows their transposed parts update stay in L2.
+#ifndef SPMM_GROUP
+#define SPMM_GROUP 2
+#endif
+
 struct SpmmArgs {
     int64_t n;
+    int64_t R;          // row blocks
     int k;
     const uint32_t *data;
     const ChunkRec *chunk;
     const int64_t *rb_chunk;
-    const int32_t *warp_rb;
-    int W;
+    int *sched;         // next row-block group to hand out
     const float *X;
     float *Y;
     int *err;
@@ -121,6 +130,22 @@ __device__ __forceinline__ void load_at(const float *T, int ks, int g, int t, ui
     split_tf32(p[4 * RS + 8], ah[3], al[3]);
 }
 
+// Offset of S[r][c] (S = L + L^T - D) in a complete diagonal chunk, whose
+// 136 entries are the lower triangle in row-major order.
+__device__ __forceinline__ int tri_off(int r, int c) {
+    const int a = max(r, c), b = min(r, c);
+    return ((a * (a + 1)) >> 1) + b;
+}
+// A fragment (slice ks) of S read straight from a complete diagonal chunk.
+__device__ __forceinline__ void load_a_tri(const float *v, int ks, int g, int t, uint32_t (&ah)[4],
+                                           uint32_t (&al)[4]) {
+    const int c = 8 * ks + t;
+    split_tf32(v[tri_off(g, c)], ah[0], al[0]);
+    split_tf32(v[tri_off(g + 8, c)], ah[1], al[1]);
+    split_tf32(v[tri_off(g, c + 4)], ah[2], al[2]);
+    split_tf32(v[tri_off(g + 8, c + 4)], ah[3], al[3]);
+}
+
 // Issue the bulk copies of one chunk into stage s (one lane).
 template <int NT>
 __device__ __forceinline__ void issue_chunk(const SpmmArgs &a, WarpSmem<NT> *ws, int4 rec, int s, uint64_t pol_stream,
@@ -148,12 +173,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
     constexpr int S = C::STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * C::WARPS + warp;
-    if (gw >= a.W) return;
     WarpSmem<NT> *ws = reinterpret_cast<WarpSmem<NT> *>(smem_raw) + warp;
-    const int rb0 = a.warp_rb[gw], rb1 = a.warp_rb[gw + 1];
-    if (rb0 >= rb1) return;
-    const int64_t c0 = a.rb_chunk[rb0], c1 = a.rb_chunk[rb1];
     const int g = lane >> 2, t = lane & 3;   // mma fragment coordinates
     const int k = a.k;
 
@@ -164,12 +184,53 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
     __syncwarp();
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
-    // lane 0 issues; the record of the chunk after next is loaded one step early
+
+    // Lane 0 is the producer.  Its cursor [ic, ic_end) walks the chunks of
+    // the row-block group in hand; `pending` holds the record of chunk ic.
+    // The next group is requested (atomic) when a group is taken up, and
+    // its chunk bounds are read one chunk later, so neither latency lands
+    // on the switch from one group to the next.
+    int64_t ic = 0, ic_end = 0, res_rb = 0, res_lo = 0, res_hi = 0;
+    int res_state = 0;   // 0: no further group, 1: requested, 2: bounds read
+    bool pend_ok = false;
     int4 pending = make_int4(0, 0, 0, 0);
+    auto request = [&]() {
+        res_rb = static_cast<int64_t>(atomicAdd(a.sched, 1)) * SPMM_GROUP;
+        res_state = 1;
+    };
+    auto resolve = [&]() {
+        if (res_state != 1) return;
+        if (res_rb >= a.R) { res_state = 0; return; }
+        res_lo = a.rb_chunk[res_rb];
+        res_hi = a.rb_chunk[res_rb + SPMM_GROUP < a.R ? res_rb + SPMM_GROUP : a.R];
+        res_state = 2;
+    };
+    auto take_group = [&]() -> bool {
+        resolve();
+        if (res_state != 2) return false;
+        ic = res_lo;
+        ic_end = res_hi;
+        request();
+        return true;
+    };
+    auto advance = [&]() {   // move the cursor to the next chunk
+        resolve();
+        if (++ic >= ic_end && !take_group()) {
+            pend_ok = false;
+            return;
+        }
+        pending = load_rec(a.chunk, ic);
+    };
+    int inflight = 0;   // lane 0: chunks issued and not yet consumed
     if (lane == 0) {
-        for (int st = 0; st < S; ++st)
-            if (c0 + st < c1) issue_chunk<NT>(a, ws, load_rec(a.chunk, c0 + st), st, pol_stream, pol_keep);
-        if (c0 + S < c1) pending = load_rec(a.chunk, c0 + S);
+        request();
+        pend_ok = take_group();
+        if (pend_ok) pending = load_rec(a.chunk, ic);
+        for (int st = 0; st < S && pend_ok; ++st) {
+            issue_chunk<NT>(a, ws, pending, st, pol_stream, pol_keep);
+            ++inflight;
+            advance();
+        }
     }
 
     float yr[NT][4];      // Y_R accumulators (D fragments)
@@ -206,13 +267,15 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         yb ^= 1;
     };
 
-    for (int64_t c = c0; c < c1; ++c) {
+    while (true) {
+        const int nfl = __shfl_sync(0xffffffffu, inflight, 0);
+        if (nfl == 0) break;
         const bool ok = mbar_wait_bounded(&ws->bar[s], (phases >> s) & 1u);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(a.err, DEV_TIMEOUT);
             // let copies already in flight land before the warp leaves
             int ss = s;
-            for (int64_t cc = c; cc < c1 && cc < c + S; ++cc) {
+            for (int q = 0; q < nfl; ++q) {
                 mbar_wait_bounded(&ws->bar[ss], (phases >> ss) & 1u);
                 ss = (ss + 1 == S) ? 0 : ss + 1;
             }
@@ -228,12 +291,14 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         const float *sval = reinterpret_cast<const float *>(ws->cd[s] + m.z);
 
         // A chunk holding all 256 entries of its off-diagonal tile is that tile
-        // in row-major order (indices unique and sorted), so its fragments
-        // are read straight from the staged values.  Any other chunk is
-        // scattered by its indices into a zeroed tile (the diagonal chunk
-        // into the symmetric S = L + L^T - D).
+        // in row-major order (indices unique and sorted), and a diagonal chunk
+        // holding all 136 entries of its lower triangle is that triangle in
+        // row-major order, so their fragments are read straight from the
+        // staged values.  Any other chunk is scattered by its indices into a
+        // zeroed tile (a diagonal one into the symmetric S = L + L^T - D).
         const bool full = !is_diag && cnt == 256;
-        if (!full) {
+        const bool tri = is_diag && cnt == TILE * (TILE + 1) / 2;   // complete diagonal tile, canonical order
+        if (!full && !tri) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int e = lane; e < TILE * HS / 4; e += 32) reinterpret_cast<float4 *>(ws->H)[e] = z;
             __syncwarp();
@@ -270,7 +335,8 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t ah[4], al[4];
-                load_a<HS>(ws->H, ks, g, t, ah, al);
+                if (tri) load_a_tri(sval, ks, g, t, ah, al);
+                else load_a<HS>(ws->H, ks, g, t, ah, al);
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
                     mma3(yr[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
@@ -325,11 +391,13 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
             reduce_tile(yc, static_cast<int64_t>(ct) * TILE, TILE);   // off-diagonal tiles lie inside 0..n-1
         }
         __syncwarp();
-        if (c + S < c1) {
-            if (lane == 0) {
+        if (lane == 0) {
+            --inflight;
+            if (pend_ok) {
                 fence_proxy_async();
                 issue_chunk<NT>(a, ws, pending, s, pol_stream, pol_keep);
-                if (c + S + 1 < c1) pending = load_rec(a.chunk, c + S + 1);
+                ++inflight;
+                advance();
             }
         }
         s = (s + 1 == S) ? 0 : s + 1;
@@ -442,8 +510,10 @@ static cudaError_t launch_tiled(const lobpcg_ctx *h, const float *X, float *Y, i
         attr_set[dev & 63] = true;
     }
     SpmmArgs a;
-    a.n = h->T.n; a.k = k; a.data = h->T.data; a.chunk = h->T.chunk; a.rb_chunk = h->T.rb_chunk;
-    a.warp_rb = h->T.warp_rb; a.W = h->T.warps; a.X = X; a.Y = Y; a.err = h->d_err;
+    a.n = h->T.n; a.R = h->T.R; a.k = k; a.data = h->T.data; a.chunk = h->T.chunk; a.rb_chunk = h->T.rb_chunk;
+    a.sched = h->T.sched; a.X = X; a.Y = Y; a.err = h->d_err;
+    cudaError_t e = cudaMemsetAsync(h->T.sched, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     const int blocks = (h->T.warps + C::WARPS - 1) / C::WARPS;
     k_spmm_sym_tiled<NT><<<blocks, C::WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();

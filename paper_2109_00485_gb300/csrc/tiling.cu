@@ -242,26 +242,14 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     TRY(cudaStreamSynchronize(s));
     std::memcpy(&h->gershgorin, &gbits, sizeof(double));
 
-    // 5. partition row blocks over the SpMM warps, balancing padded entries
-    //    plus a per-chunk and per-row-block overhead
+    // 5. SpMM residency (warps hand out row-block groups among themselves
+    //    through the work counter) and the counter itself
 #ifndef SPMM_WARPS_PER_SM
 #define SPMM_WARPS_PER_SM 16
 #endif
     const int64_t want = static_cast<int64_t>(h->num_sms) * SPMM_WARPS_PER_SM;
-    const int W = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, R)));
-    std::vector<int32_t> warp_rb(W + 1);
-    auto cost = [&](int64_t r) { return rb_nnz[r] + 32 * rb_chunk[r] + 64 * r; };
-    const double total = static_cast<double>(cost(R));
-    int64_t r = 0;
-    for (int w = 0; w <= W; ++w) {
-        if (w == W) { warp_rb[w] = static_cast<int32_t>(R); break; }
-        const double target = total * w / W;
-        while (r < R && static_cast<double>(cost(r)) < target) ++r;
-        warp_rb[w] = static_cast<int32_t>(r);
-    }
-    T.warps = W;
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.warp_rb), sizeof(int32_t) * (W + 1)));
-    TRY(cudaMemcpyAsync(T.warp_rb, warp_rb.data(), sizeof(int32_t) * (W + 1), cudaMemcpyHostToDevice, s));
+    T.warps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, R)));
+    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.sched), sizeof(int) * 4));
 
     TRY(cudaFreeAsync(d_rowsum, s));
     TRY(cudaFreeAsync(d_rb_nnz, s));
