@@ -75,6 +75,73 @@ __global__ void k_resid(int64_t n, int k, const T *X, const T *HX, const double 
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) atomicAdd(&norms[q], red[q]);
 }
 
+// Residual of the mixed-precision refinement: X, HX float64, W float32.
+// r = HX - x theta and the norms in float64 (the cancellation happens here);
+// W = r (mode 0) or r / g(d - theta) (mode 1) rounded to float32: W is a
+// search direction and needs no more.  R32 (may be NULL) = float32(r).
+__global__ void k_resid_mixed(int64_t n, int k, const double *X, const double *HX, const double *theta,
+                              const float *d, float *W, float *R32, int mode, double *norms) {
+    extern __shared__ double red[];   // [2k]
+    const int per = blockDim.x / k;
+    const int j = threadIdx.x % k;
+    const bool active = threadIdx.x < per * k;
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) red[q] = 0.0;
+    __syncthreads();
+    double rr = 0.0, xx = 0.0;
+    const double th = theta[j];
+    const float thf = static_cast<float>(th);
+    const float delta = 1e-3f * fmaxf(1.f, fabsf(thf));
+    if (active) {
+        const int64_t stride = static_cast<int64_t>(gridDim.x) * per;
+        for (int64_t i = static_cast<int64_t>(blockIdx.x) * per + threadIdx.x / k; i < n; i += stride) {
+            const int64_t e = i * k + j;
+            const double x = X[e];
+            const double r = fma(-x, th, HX[e]);
+            rr = fma(r, r, rr);
+            xx = fma(x, x, xx);
+            float w = static_cast<float>(r);
+            if (R32) R32[e] = w;
+            if (mode == 1) {
+                const float t = static_cast<float>(static_cast<double>(d[i]) - th);
+                const float g = (t >= 0.f) ? fmaxf(t, delta) : -fmaxf(-t, delta);
+                w = w / g;
+            }
+            W[e] = w;
+        }
+        atomicAdd(&red[j], rr);
+        atomicAdd(&red[k + j], xx);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) atomicAdd(&norms[q], red[q]);
+}
+
+// Z (n x k, float64, in place) <- Z C + A, C k x k float64 row-major, A
+// float32 n x k; Z32 = float32(Z).  The X and HX updates of the mixed
+// refinement: Z C carries the converged part in float64, A = [W P] C_23
+// (the new P, or HP) the float32 correction.
+__global__ void k_xupdate(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32) {
+    extern __shared__ double sx[];    // C (k x k), then `per` rows of Z
+    double *sC = sx, *sZ = sx + k * k;
+    const int per = blockDim.x / k;
+    const int r = threadIdx.x / k, j = threadIdx.x % k;
+    const bool active = threadIdx.x < per * k;
+    for (int q = threadIdx.x; q < k * k; q += blockDim.x) sC[q] = C[q];
+    for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * per; i0 < n; i0 += static_cast<int64_t>(gridDim.x) * per) {
+        const int rows = static_cast<int>(n - i0 < per ? n - i0 : per);
+        __syncthreads();
+        if (active && r < rows) sZ[threadIdx.x] = Z[i0 * k + threadIdx.x];
+        __syncthreads();
+        if (active && r < rows) {
+            double acc = 0.0;
+            for (int l = 0; l < k; ++l) acc = fma(sZ[r * k + l], sC[l * k + j], acc);
+            const int64_t e = (i0 + r) * k + j;
+            acc += static_cast<double>(A[e]);
+            Z[e] = acc;
+            Z32[e] = static_cast<float>(acc);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Gram
 
 constexpr int GR_ROWS = 64;     // rows staged per pass
@@ -950,6 +1017,29 @@ cudaError_t launch_resid(int64_t n, int k, const T *X, const T *HX, const double
     int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
     if (blocks < 1) blocks = 1;
     k_resid<T><<<blocks, threads, sizeof(double) * 2 * k, s>>>(n, k, X, HX, theta, d, W, mode, norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_mixed(int64_t n, int k, const double *X, const double *HX, const double *theta,
+                               const float *d, float *W, float *R32, int mode, double *norms, int num_sms,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * k, s);
+    if (e != cudaSuccess) return e;
+    const int threads = (256 / k) * k;
+    const int64_t per = threads / k;
+    int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
+    if (blocks < 1) blocks = 1;
+    k_resid_mixed<<<blocks, threads, sizeof(double) * 2 * k, s>>>(n, k, X, HX, theta, d, W, R32, mode, norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xupdate(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
+                           cudaStream_t s) {
+    const int threads = (256 / k) * k;
+    const int64_t per = threads / k;
+    int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
+    if (blocks < 1) blocks = 1;
+    k_xupdate<<<blocks, threads, sizeof(double) * (k * k + threads), s>>>(n, k, Z, C, A, Z32);
     return cudaGetLastError();
 }
 

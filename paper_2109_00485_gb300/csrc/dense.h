@@ -27,6 +27,13 @@ struct CombineOut {
 template <typename T>
 cudaError_t launch_resid(int64_t n, int k, const T *X, const T *HX, const double *theta, const float *d, T *W,
                          int mode, double *norms, int num_sms, cudaStream_t s);
+// Mixed-precision refinement: float64 residual into a float32 W, and the
+// float64 X / HX update Z <- Z C + A (A float32) with a float32 copy of Z.
+cudaError_t launch_resid_mixed(int64_t n, int k, const double *X, const double *HX, const double *theta,
+                               const float *d, float *W, float *R32, int mode, double *norms, int num_sms,
+                               cudaStream_t s);
+cudaError_t launch_xupdate(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
+                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmBlocks<T> b, double *M, int num_sms,
                         cudaStream_t s);

