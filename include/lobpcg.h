@@ -179,8 +179,9 @@ LOBPCG_API lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double
  *           (needs params.precond == 2 at create, else ERR_UNSUPPORTED)
  *   mode 3: the learned tile network (needs params.precond == 3 at create
  *           and weights from lobpcg_precond_train or lobpcg_mlp_set_params);
- *           k <= params.k.  A correction entry that is not finite is
- *           dropped (that entry keeps its mode-1 value).
+ *           k <= params.k.  A tile column whose correction is not finite
+ *           keeps its mode-1 value; a correction longer (over the tile) than
+ *           the mode-1 value is scaled down to that length.
  *   R, W  : float32 n x k row-major, device (may be the same buffer)
  *   theta : float64[k], device
  */

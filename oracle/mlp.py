@@ -88,8 +88,10 @@ def tile_target(y: np.ndarray, r: np.ndarray, d: np.ndarray, theta: float, normG
 
 
 def apply(p: dict, R: np.ndarray, d: np.ndarray, theta: np.ndarray, normG: float) -> np.ndarray:
-    """w_T = D_theta^{-1} r_T + (s / g) MLP(x) for every 64-row tile and column
-    (a ragged last tile is zero-padded; tiles with s = 0 give w_T = 0).
+    """w_T = D_theta^{-1} r_T + c_T, c_T = (s / g) MLP(x), for every 64-row tile
+    and column (a ragged last tile is zero-padded; tiles with s = 0 give
+    w_T = 0).  A non-finite c_T is dropped; a c_T longer than D_theta^{-1} r_T
+    is scaled down to its length.
     Pinned through its pieces: the forward pass by the gradient checks, the
     diagonal part by apply_diag's own pins, and a zero output layer giving
     exactly the diagonal solve."""
@@ -106,5 +108,9 @@ def apply(p: dict, R: np.ndarray, d: np.ndarray, theta: np.ndarray, normG: float
             if s == 0.0:
                 continue
             y, _ = forward(p, x[None, :])
-            W[t0:t0 + m, j] += (s / normG) * y[0, :m]
+            c = (s / normG) * y[0, :m]
+            if not np.all(np.isfinite(c)):
+                continue
+            cn, dn = np.linalg.norm(c), np.linalg.norm(W[t0:t0 + m, j])
+            W[t0:t0 + m, j] += c * (dn / cn if cn > dn else 1.0)
     return W

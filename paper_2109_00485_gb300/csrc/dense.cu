@@ -246,6 +246,165 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram(int64_t n, int k, int na, G
         }
 }
 
+// ---------------------------------------------------------------- Gram on the tensor cores
+
+// M (ma x mb) += A^T B for float32 blocks with k % 4 == 0, ma <= 96,
+// mb <= 192, on the tensor cores: mma.sync m16n8k8 TF32 with the 3-term
+// split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (FP32-level products).
+// A CTA stages 64-row tiles of [A_0..] and [B_0..] side by side in shared
+// memory (cp.async, two stages; row strides = 24 mod 32 words, so fragment
+// loads are free of bank conflicts).  Warp w owns output M-tile w % MT and
+// N-tiles w / MT + WN t; each 64-row tile's products start from zero and are
+// added to Kahan-compensated FP32 sums, FP64 across CTAs (as k_gram).
+constexpr int GT_ROWS = 64;
+
+__device__ __forceinline__ int gt_stride(int cols) {   // >= cols, = 24 (mod 32)
+    int s = cols + ((24 - cols % 32) + 32) % 32;
+    return s;
+}
+
+// Round to TF32 (10 stored mantissa bits), to nearest with ties away from
+// zero, by integer arithmetic on the bit pattern (two ALU operations).
+__device__ __forceinline__ uint32_t gt_tf32(float x) {
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+__device__ __forceinline__ void gt_split(float x, uint32_t &hi, uint32_t &lo) {
+    hi = gt_tf32(x);
+    lo = gt_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void gt_mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                       uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void gt_cp16(void *dst, const void *src, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const int sz = valid ? 16 : 0;   // 0: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+
+// GT_TPW: most N-tiles per warp (1, 2 or 4)
+template <int GT_TPW>
+__global__ void __launch_bounds__(384) k_gram_tc(int64_t n, int k, int na, GemmBlocks<float> a, int nb,
+                                                 GemmBlocks<float> b, double *M, int MT, int NT, int WN) {
+    extern __shared__ __align__(16) float gsm[];
+    const int ma = na * k, mb = nb * k;
+    const int SA = gt_stride(16 * MT), SB = gt_stride(8 * NT);
+    auto stA = [&](int st) { return gsm + st * GT_ROWS * SA; };
+    auto stB = [&](int st) { return gsm + 2 * GT_ROWS * SA + st * GT_ROWS * SB; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int mi = warp % MT, nj0 = warp / MT;
+    // zero the padding columns of both stages once (cp.async never writes them)
+    for (int e = threadIdx.x; e < 2 * GT_ROWS * (SA - ma); e += blockDim.x) {
+        const int st = e / (GT_ROWS * (SA - ma)), q = e % (GT_ROWS * (SA - ma));
+        stA(st)[(q / (SA - ma)) * SA + ma + q % (SA - ma)] = 0.f;
+    }
+    for (int e = threadIdx.x; e < 2 * GT_ROWS * (SB - mb); e += blockDim.x) {
+        const int st = e / (GT_ROWS * (SB - mb)), q = e % (GT_ROWS * (SB - mb));
+        stB(st)[(q / (SB - mb)) * SB + mb + q % (SB - mb)] = 0.f;
+    }
+    const int kv = k / 4;   // 16-byte pieces per row of a block
+    // this thread's first (row, piece) of a block tile and the stride of the
+    // walk (no divisions inside the copy loops)
+    const int r_start = threadIdx.x / kv, c_start = threadIdx.x % kv;
+    const int dr = blockDim.x / kv, dc = blockDim.x % kv;
+    auto stage = [&](int st, int64_t r0) {
+        for (int blk = 0; blk < na + nb; ++blk) {
+            const bool isA = blk < na;
+            const float *src0 = isA ? a.p[blk] : b.p[blk - na];
+            float *dst0 = isA ? stA(st) + blk * k : stB(st) + (blk - na) * k;
+            const int S = isA ? SA : SB;
+            int r = r_start, c4 = c_start;
+            while (r < GT_ROWS) {
+                const int64_t row = r0 + r;
+                const bool valid = row < n;
+                gt_cp16(dst0 + r * S + 4 * c4, src0 + (valid ? row : 0) * k + 4 * c4, valid);
+                r += dr;
+                c4 += dc;
+                if (c4 >= kv) {
+                    c4 -= kv;
+                    ++r;
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float sum[GT_TPW][4], cmp[GT_TPW][4];
+#pragma unroll
+    for (int u = 0; u < GT_TPW; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sum[u][c] = cmp[u][c] = 0.f;
+    const int64_t ntile = (n + GT_ROWS - 1) / GT_ROWS;
+    int64_t tile = blockIdx.x;
+    if (tile < ntile) stage(0, tile * GT_ROWS);
+    int cur = 0;
+    for (; tile < ntile; tile += gridDim.x) {
+        const int64_t nxt = tile + gridDim.x;
+        if (nxt < ntile) {
+            stage(cur ^ 1, nxt * GT_ROWS);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float *sA = stA(cur), *sB = stB(cur);
+        float part[GT_TPW][4];
+#pragma unroll
+        for (int u = 0; u < GT_TPW; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[u][c] = 0.f;
+#pragma unroll 2
+        for (int ks = 0; ks < GT_ROWS / 8; ++ks) {
+            // A fragment of (A^T)[16 mi + .., 8 ks + ..]: element (m, kk) = sA[kk][16 mi + m]
+            const float *pa = sA + (8 * ks + t) * SA + 16 * mi + g;
+            uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3;
+            gt_split(pa[0], ah0, al0);
+            gt_split(pa[8], ah1, al1);
+            gt_split(pa[4 * SA], ah2, al2);
+            gt_split(pa[4 * SA + 8], ah3, al3);
+#pragma unroll
+            for (int u = 0; u < GT_TPW; ++u) {
+                const int nj = nj0 + WN * u;
+                if (nj < NT) {
+                    // B fragment: b0 = B[8 ks + t][8 nj + g], b1 = B[8 ks + t + 4][8 nj + g]
+                    const float *pb = sB + (8 * ks + t) * SB + 8 * nj + g;
+                    uint32_t bh0, bl0, bh1, bl1;
+                    gt_split(pb[0], bh0, bl0);
+                    gt_split(pb[4 * SB], bh1, bl1);
+                    gt_mma(part[u], al0, al1, al2, al3, bh0, bh1);
+                    gt_mma(part[u], ah0, ah1, ah2, ah3, bl0, bl1);
+                    gt_mma(part[u], ah0, ah1, ah2, ah3, bh0, bh1);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GT_TPW; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float y = part[u][c] - cmp[u][c];
+                const float tt = sum[u][c] + y;
+                cmp[u][c] = (tt - sum[u][c]) - y;
+                sum[u][c] = tt;
+            }
+        __syncthreads();   // stage `cur` is refilled next
+        cur ^= 1;
+    }
+#pragma unroll
+    for (int u = 0; u < GT_TPW; ++u) {
+        const int nj = nj0 + WN * u;
+        if (nj >= NT) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int ia = 16 * mi + g + (c >= 2 ? 8 : 0), ib = 8 * nj + 2 * t + (c & 1);
+            if (ia < ma && ib < mb)
+                atomicAdd(&M[ia * mb + ib], static_cast<double>(sum[u][c]) - static_cast<double>(cmp[u][c]));
+        }
+    }
+}
+
 // ---------------------------------------------------------------- combine
 
 // Four consecutive values from shared memory (16-byte loads; p 16-byte aligned).
@@ -584,8 +743,9 @@ __device__ int cta_jacobi(double *A, double *V, int m, double *cs, int *pairs, i
 // destroyed), FP64, one CTA (m <= 96, k <= 32):
 //   1. Householder tridiagonalisation A = Q T Q^T (Golub & Van Loan,
 //      Section 8.3.1); the reflectors stay in A's lower triangle.
-//   2. Eigenvalue i of T by bisection on the Sturm count (the number of
-//      negative pivots of T - x I), one thread per eigenvalue.
+//   2. Eigenvalue i of T by multisection on the Sturm count (the number of
+//      negative pivots of T - x I): float32 with 32 points per eigenvalue,
+//      then float64 with all k eigenvalues packed into one warp.
 //   3. Its eigenvector by inverse iteration: tridiagonal LU with partial
 //      pivoting of T - w_i I, three solves from distinct start vectors.
 //      Vectors of eigenvalues closer than 1e-10 ||T|| are re-orthogonalised.
@@ -596,6 +756,8 @@ constexpr int EIG_MAXM = 96;
 __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V, double *d, double *e,
                                   double *tau, double *pv) {
     __shared__ double red_s, tnorm;
+    __shared__ double blo[32], bhi[32], e2[EIG_MAXM];
+    __shared__ float df[EIG_MAXM], e2f[EIG_MAXM];
     // 1. tridiagonalisation (reductions by warps, updates by all threads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     __shared__ double kk_s;
@@ -666,6 +828,13 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
         }
         tnorm = tn;
     }
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        df[r] = static_cast<float>(d[r]);
+        if (r + 1 < m) {
+            e2[r] = e[r] * e[r];
+            e2f[r] = static_cast<float>(e2[r]);
+        }
+    }
     __syncthreads();
     // 2. eigenvalue estimates by float32 multisection: one warp per wanted
     //    eigenvalue, its 32 lanes count the eigenvalues below 32 points of the
@@ -677,12 +846,11 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
         for (int it = 0; it < 8 && fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f; ++it) {
             const float x = flo + (fhi - flo) * static_cast<float>(lane + 1) / 33.f;
             int cnt = 0;
-            float q = static_cast<float>(d[0]) - x;
+            float q = df[0] - x;
             cnt += q < 0.f;
             for (int r = 1; r < m; ++r) {
                 if (fabsf(q) < 1e-30f) q = (q < 0.f) ? -1e-30f : 1e-30f;
-                const float er = static_cast<float>(e[r - 1]);
-                q = (static_cast<float>(d[r]) - x) - __fdividef(er * er, q);
+                q = (df[r] - x) - __fdividef(e2f[r - 1], q);
                 cnt += q < 0.f;
             }
             // lanes whose point has more than i eigenvalues below it bound from above
@@ -693,34 +861,54 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             flo = nlo;
             fhi = nhi;
         }
-        // float64 multisection from the float32 bracket, widened by the
-        // float32 count uncertainty; the pivot reciprocal is a float32 seed
-        // refined by one Newton step (relative error ~1e-14, enough for signs)
-        double lo = static_cast<double>(flo), hi = static_cast<double>(fhi);
-        const double pad = 1e-5 * tnorm + 1e-300;
-        lo = fmax(-tnorm, lo - pad);
-        hi = fmin(tnorm, hi + pad);
-        for (int it = 0; it < 12 && hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
-            const double x = lo + (hi - lo) * static_cast<double>(lane + 1) / 33.0;
-            int cnt = 0;
-            double q = d[0] - x;
-            cnt += q < 0.0;
-            for (int r = 1; r < m; ++r) {
-                if (fabs(q) < 1e-280) q = (q < 0.0) ? -1e-280 : 1e-280;
-                double rc = static_cast<double>(__frcp_rn(static_cast<float>(q)));
-                if (!isfinite(rc)) rc = 1.0 / q;   // outside float range
-                rc = rc * (2.0 - q * rc);
-                q = (d[r] - x) - e[r - 1] * e[r - 1] * rc;
-                cnt += q < 0.0;
-            }
-            const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
-            const int first = above ? (__ffs(above) - 1) : 32;
-            const double nlo = (first == 0) ? lo : lo + (hi - lo) * static_cast<double>(first) / 33.0;
-            const double nhi = (first == 32) ? hi : lo + (hi - lo) * static_cast<double>(first + 1) / 33.0;
-            lo = nlo;
-            hi = nhi;
+        // the float32 bracket, widened by the float32 count uncertainty
+        if (lane == 0) {
+            const double pad = 1e-5 * tnorm + 1e-300;
+            blo[i] = fmax(-tnorm, static_cast<double>(flo) - pad);
+            bhi[i] = fmin(tnorm, static_cast<double>(fhi) + pad);
         }
-        if (lane == 0) w[i] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    // float64 multisection of all k brackets by warp 0 at once: eigenvalue
+    // i takes npts = 32 / k lanes, each counting below one interior point.
+    // (GB300 issues a float64 warp instruction over many cycles, so the
+    // float64 work is packed into as few warp instructions as possible.)
+    // The pivot reciprocal is a float32 seed refined by one Newton step
+    // (relative error ~1e-14, enough for the signs).
+    if (warp == 0) {
+        const int npts = 32 / k;
+        const int i = lane / npts, jp = lane % npts;
+        const bool act = i < k;
+        double lo = act ? blo[i] : 0.0, hi = act ? bhi[i] : 0.0;
+        for (int it = 0; it < 80; ++it) {
+            const bool done = !act || !(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300);
+            if (__all_sync(0xffffffffu, done)) break;
+            const double x = lo + (hi - lo) * static_cast<double>(jp + 1) / static_cast<double>(npts + 1);
+            int cnt = 0;
+            if (act) {
+                double q = d[0] - x;
+                cnt += q < 0.0;
+                for (int r = 1; r < m; ++r) {
+                    if (fabs(q) < 1e-280) q = (q < 0.0) ? -1e-280 : 1e-280;
+                    double rc = static_cast<double>(__frcp_rn(static_cast<float>(q)));
+                    if (!isfinite(rc)) rc = 1.0 / q;   // outside float range
+                    rc = rc * (2.0 - q * rc);
+                    q = (d[r] - x) - e2[r - 1] * rc;
+                    cnt += q < 0.0;
+                }
+            }
+            const unsigned above = __ballot_sync(0xffffffffu, act && cnt > i);
+            if (act && !done) {
+                const unsigned grp = (above >> (i * npts)) & ((npts == 32) ? 0xffffffffu : ((1u << npts) - 1u));
+                const int first = grp ? (__ffs(grp) - 1) : npts;   // first point with cnt > i
+                const double w0 = hi - lo;
+                const double nlo = (first == 0) ? lo : lo + w0 * static_cast<double>(first) / (npts + 1);
+                const double nhi = (first == npts) ? hi : lo + w0 * static_cast<double>(first + 1) / (npts + 1);
+                lo = nlo;
+                hi = nhi;
+            }
+        }
+        if (act && jp == 0) w[i] = 0.5 * (lo + hi);
     }
     __syncthreads();
     // 3. eigenvector by inverse iteration in float64, one thread per pair;
@@ -1049,6 +1237,38 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
     const int ma = na * k, mb = nb * k;
     cudaError_t e = cudaMemsetAsync(M, 0, sizeof(double) * ma * mb, s);
     if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+        bool aligned = true;
+        for (int q = 0; q < na; ++q) aligned = aligned && (reinterpret_cast<uintptr_t>(a.p[q]) & 15u) == 0;
+        for (int q = 0; q < nb; ++q) aligned = aligned && (reinterpret_cast<uintptr_t>(b.p[q]) & 15u) == 0;
+        const int MT = (ma + 15) / 16, NT = (mb + 7) / 8;
+        const int WN = std::min(NT, (MT == 5) ? 2 : std::max(1, 12 / MT));   // warps per M-tile
+        const int tpw = (NT + WN - 1) / WN;
+        if (k % 4 == 0 && aligned && ma <= 96 && mb <= 192 && tpw <= 4) {
+            const int W = MT * WN;
+            auto stride = [](int cols) { return cols + ((24 - cols % 32) + 32) % 32; };
+            const size_t smem = sizeof(float) * 2 * GT_ROWS * (stride(16 * MT) + stride(8 * NT));
+            static bool attr = false;
+            if (!attr) {
+                e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            const int64_t ntile = (n + GT_ROWS - 1) / GT_ROWS;
+            // CTAs per SM: as many as shared memory allows, up to 4
+            const int per_sm = std::max(1, std::min<int>(4, static_cast<int>((200 * 1024) / smem)));
+            int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * per_sm));
+            if (blocks < 1) blocks = 1;
+            if (tpw == 1) k_gram_tc<1><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
+            else if (tpw == 2) k_gram_tc<2><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
+            else k_gram_tc<4><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = sizeof(T) * GR_ROWS * (ma + mb);
     const int64_t ntile = (n + GR_ROWS - 1) / GR_ROWS;   // one tile per block pass
     int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * 4));

@@ -191,22 +191,48 @@ __device__ __forceinline__ float diag_solve(float r, float d, double th) {
     return r / g;
 }
 
-// W = D^{-1} R + (s/g) y for every pair; a non-finite correction is dropped
-// (that entry keeps the diagonal solve).
+// W = D^{-1} R + c for every pair (tile, column), c = (s/g) y the network's
+// correction: a non-finite correction is dropped, and one whose norm over the
+// tile exceeds that of the tile's diagonal solve is scaled down to it, so the
+// learned form stays within a factor 2 of the diagonal one.  One warp per
+// pair, two rows per lane.
 __global__ void k_mlp_outputs(int64_t n, int k, const float *Y, const float *sc, double normG, const float *R,
                               const float *d, const double *theta, float *W) {
+    const int lane = threadIdx.x & 31;
     const int64_t P = ((n + MLP_TILE - 1) / MLP_TILE) * k;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P * MLP_TILE;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t p = e / MLP_TILE;
-        const int i = static_cast<int>(e % MLP_TILE);
+    for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < P;
+         p += (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5) {
         const int64_t t = p / k;
         const int j = static_cast<int>(p % k);
-        const int64_t row = t * MLP_TILE + i;
-        if (row >= n) continue;
-        const float c = static_cast<float>(sc[p] / normG) * Y[p * MLP_NOUT + i];
-        const float w = diag_solve(R[row * k + j], d[row], theta[j]);
-        W[row * k + j] = isfinite(c) ? w + c : w;
+        const float f = static_cast<float>(sc[p] / normG);
+        float c[2], wd[2];
+        float cc = 0.f, dd = 0.f;
+        bool finite = true;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t row = t * MLP_TILE + lane + 32 * h;
+            c[h] = 0.f;
+            wd[h] = 0.f;
+            if (row < n) {
+                c[h] = f * Y[p * MLP_NOUT + lane + 32 * h];
+                wd[h] = diag_solve(R[row * k + j], d[row], theta[j]);
+                finite = finite && isfinite(c[h]);
+                cc += c[h] * c[h];
+                dd += wd[h] * wd[h];
+            }
+        }
+        finite = __all_sync(0xffffffffu, finite);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cc += __shfl_xor_sync(0xffffffffu, cc, o);
+            dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        }
+        const float scale = !finite ? 0.f : (cc > dd ? sqrtf(dd / cc) : 1.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t row = t * MLP_TILE + lane + 32 * h;
+            if (row < n) W[row * k + j] = finite ? wd[h] + scale * c[h] : wd[h];
+        }
     }
 }
 
@@ -540,7 +566,7 @@ cudaError_t mlp_apply(lobpcg_ctx *h, int k, const float *R, const double *theta,
     if (e != cudaSuccess) return e;
     e = forward(h, Xin, P, Hh, Y, s);
     if (e != cudaSuccess) return e;
-    k_mlp_outputs<<<grid_for(P * MLP_TILE, h->num_sms), 256, 0, s>>>(n, k, Y, sc, h->gershgorin, R, h->T.diag, theta, W);
+    k_mlp_outputs<<<grid_for(P * 32, h->num_sms), 256, 0, s>>>(n, k, Y, sc, h->gershgorin, R, h->T.diag, theta, W);
     return cudaGetLastError();
 }
 

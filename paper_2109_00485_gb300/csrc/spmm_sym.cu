@@ -82,10 +82,10 @@ struct SpmmArgs {
     int *err;
 };
 
+// Round to TF32 (10 stored mantissa bits), to nearest with ties away from
+// zero, by integer arithmetic on the bit pattern (two ALU operations).
 __device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
     hi = to_tf32(x);
