@@ -285,6 +285,38 @@ __device__ __forceinline__ void gt_cp16(void *dst, const void *src, bool valid) 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
 }
 
+__device__ __forceinline__ void gt_cp16s(uint32_t dst, const void *src, bool valid) {
+    const int sz = valid ? 16 : 0;   // 0: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(sz) : "memory");
+}
+
+// Copy rows [r0, r0 + 64) of every block into stage `stA_off`/`stB_off`
+// (float offsets of the stage's A and B regions); rows past n are zeroed.
+__device__ __forceinline__ void gt_stage(const float *const *bp, const int *bcol, int nblk, int na, int SA, int SB,
+                                         int stA_off, int stB_off, uint32_t sbase, int64_t n, int64_t r0, int k,
+                                         int kv, int r_start, int c_start, int dr, int dc) {
+    for (int q = 0; q < nblk; ++q) {
+        const float *src0 = bp[q];
+        const bool isA = q < na;
+        const int S = isA ? SA : SB;
+        const uint32_t dst0 = sbase + 4u * static_cast<uint32_t>(bcol[q] + (isA ? stA_off : stB_off));
+        int r = r_start, c4 = c_start;
+        while (r < GT_ROWS) {
+            const int64_t row = r0 + r;
+            const bool valid = row < n;
+            gt_cp16s(dst0 + 4u * static_cast<uint32_t>(r * S + 4 * c4), src0 + (valid ? row : 0) * k + 4 * c4,
+                     valid);
+            r += dr;
+            c4 += dc;
+            if (c4 >= kv) {
+                c4 -= kv;
+                ++r;
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // GT_TPW: most N-tiles per warp (1, 2 or 4)
 template <int GT_TPW>
 __global__ void __launch_bounds__(384) k_gram_tc(int64_t n, int k, int na, GemmBlocks<float> a, int nb,
@@ -292,65 +324,56 @@ __global__ void __launch_bounds__(384) k_gram_tc(int64_t n, int k, int na, GemmB
     extern __shared__ __align__(16) float gsm[];
     const int ma = na * k, mb = nb * k;
     const int SA = gt_stride(16 * MT), SB = gt_stride(8 * NT);
-    auto stA = [&](int st) { return gsm + st * GT_ROWS * SA; };
-    auto stB = [&](int st) { return gsm + 2 * GT_ROWS * SA + st * GT_ROWS * SB; };
+    float *const stA0 = gsm, *const stB0 = gsm + 2 * GT_ROWS * SA;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     const int mi = warp % MT, nj0 = warp / MT;
+    // block pointers and their shared-memory destinations (column offsets)
+    __shared__ const float *bp[12];
+    __shared__ int bcol[12];
+    if (threadIdx.x < na + nb) {
+        const int q = threadIdx.x;
+        bp[q] = q < na ? a.p[q] : b.p[q - na];
+        bcol[q] = q < na ? q * k : 2 * GT_ROWS * SA + (q - na) * k;   // offset from gsm (stage 0)
+    }
     // zero the padding columns of both stages once (cp.async never writes them)
     for (int e = threadIdx.x; e < 2 * GT_ROWS * (SA - ma); e += blockDim.x) {
         const int st = e / (GT_ROWS * (SA - ma)), q = e % (GT_ROWS * (SA - ma));
-        stA(st)[(q / (SA - ma)) * SA + ma + q % (SA - ma)] = 0.f;
+        stA0[st * GT_ROWS * SA + (q / (SA - ma)) * SA + ma + q % (SA - ma)] = 0.f;
     }
     for (int e = threadIdx.x; e < 2 * GT_ROWS * (SB - mb); e += blockDim.x) {
         const int st = e / (GT_ROWS * (SB - mb)), q = e % (GT_ROWS * (SB - mb));
-        stB(st)[(q / (SB - mb)) * SB + mb + q % (SB - mb)] = 0.f;
+        stB0[st * GT_ROWS * SB + (q / (SB - mb)) * SB + mb + q % (SB - mb)] = 0.f;
     }
+    __syncthreads();
     const int kv = k / 4;   // 16-byte pieces per row of a block
     // this thread's first (row, piece) of a block tile and the stride of the
     // walk (no divisions inside the copy loops)
     const int r_start = threadIdx.x / kv, c_start = threadIdx.x % kv;
     const int dr = blockDim.x / kv, dc = blockDim.x % kv;
-    auto stage = [&](int st, int64_t r0) {
-        for (int blk = 0; blk < na + nb; ++blk) {
-            const bool isA = blk < na;
-            const float *src0 = isA ? a.p[blk] : b.p[blk - na];
-            float *dst0 = isA ? stA(st) + blk * k : stB(st) + (blk - na) * k;
-            const int S = isA ? SA : SB;
-            int r = r_start, c4 = c_start;
-            while (r < GT_ROWS) {
-                const int64_t row = r0 + r;
-                const bool valid = row < n;
-                gt_cp16(dst0 + r * S + 4 * c4, src0 + (valid ? row : 0) * k + 4 * c4, valid);
-                r += dr;
-                c4 += dc;
-                if (c4 >= kv) {
-                    c4 -= kv;
-                    ++r;
-                }
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
+    const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(gsm));
     float sum[GT_TPW][4], cmp[GT_TPW][4];
 #pragma unroll
     for (int u = 0; u < GT_TPW; ++u)
 #pragma unroll
         for (int c = 0; c < 4; ++c) sum[u][c] = cmp[u][c] = 0.f;
     const int64_t ntile = (n + GT_ROWS - 1) / GT_ROWS;
+    const int nblk = na + nb;
     int64_t tile = blockIdx.x;
-    if (tile < ntile) stage(0, tile * GT_ROWS);
+    if (tile < ntile)
+        gt_stage(bp, bcol, nblk, na, SA, SB, 0, 0, sbase, n, tile * GT_ROWS, k, kv, r_start, c_start, dr, dc);
     int cur = 0;
     for (; tile < ntile; tile += gridDim.x) {
         const int64_t nxt = tile + gridDim.x;
         if (nxt < ntile) {
-            stage(cur ^ 1, nxt * GT_ROWS);
+            gt_stage(bp, bcol, nblk, na, SA, SB, (cur ^ 1) * GT_ROWS * SA, (cur ^ 1) * GT_ROWS * SB, sbase, n,
+                     nxt * GT_ROWS, k, kv, r_start, c_start, dr, dc);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        const float *sA = stA(cur), *sB = stB(cur);
+        const float *sA = stA0 + cur * GT_ROWS * SA, *sB = stB0 + cur * GT_ROWS * SB;
         float part[GT_TPW][4];
 #pragma unroll
         for (int u = 0; u < GT_TPW; ++u)
