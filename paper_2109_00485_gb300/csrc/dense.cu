@@ -522,15 +522,21 @@ __global__ void k_coef_to_float(int n0, const double *C0, const double *C1, int 
 }
 
 // float32, K in {8, 16, 20}: each thread keeps column j of both coefficient
-// matrices in registers and walks rows; the staged A row is read with
-// 16-byte broadcast loads (a row group of K threads reads the same row).
-// Output 1, when present, starts at block 1 (c0 = K).  Semantics as k_combine.
+// matrices in registers and walks rows; 64-row tiles of the NA blocks are
+// staged by cp.async into two alternating buffers (the next tile loads while
+// this one is combined) and read with 16-byte broadcast loads (a row group
+// of K threads reads the same row).  Output 1, when present, starts at
+// block 1 (c0 = K).  Column norms: float32 per thread and tile, float64
+// across tiles.  Semantics as k_combine.
+constexpr int CR_ROWS = 64;
+
 template <int K, int NA>
 __global__ void __launch_bounds__(128) k_combine_reg(int64_t n, GemmBlocks<float> a, int nout, CombineOut<float> out,
                                                      double *colsq) {
-    __shared__ __align__(16) float sa[NA * CB_ROWS * K];
+    __shared__ __align__(16) float sa[2][NA * CR_ROWS * K];
     __shared__ double red[K];
     constexpr int G = 128 / K;   // row groups
+    constexpr int PV = CR_ROWS * K / 4;   // 16-byte pieces per block tile
     const int j = threadIdx.x % K, grp = threadIdx.x / K;
     const bool act = grp < G;
     float c0[NA * K], c1[NA * K];
@@ -540,47 +546,68 @@ __global__ void __launch_bounds__(128) k_combine_reg(int64_t n, GemmBlocks<float
         c1[c] = (nout > 1 && c >= K) ? out.Cf[NA * K * K + (c - K) * K + j] : 0.f;
     }
     for (int q = threadIdx.x; q < K; q += blockDim.x) red[q] = 0.0;
+    auto stage = [&](int st, int64_t r0) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+            for (int e = threadIdx.x; e < PV; e += blockDim.x) {
+                const int r = (4 * e) / K;
+                const bool valid = r0 + r < n;
+                gt_cp16(&sa[st][q * CR_ROWS * K + 4 * e], a.p[q] + (valid ? r0 * K + 4 * e : 0), valid);
+            }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     double nsq = 0.0;
-    const int64_t ntile = (n + CB_ROWS - 1) / CB_ROWS;
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t r0 = tile * CB_ROWS;
-        const int rows = static_cast<int>(n - r0 < CB_ROWS ? n - r0 : CB_ROWS);
+    const int64_t ntile = (n + CR_ROWS - 1) / CR_ROWS;
+    int64_t tile = blockIdx.x;
+    if (tile < ntile) stage(0, tile * CR_ROWS);
+    int cur = 0;
+    for (; tile < ntile; tile += gridDim.x) {
+        const int64_t nxt = tile + gridDim.x;
+        if (nxt < ntile) {
+            stage(cur ^ 1, nxt * CR_ROWS);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
         __syncthreads();
+        const int64_t r0 = tile * CR_ROWS;
+        const int rows = static_cast<int>(n - r0 < CR_ROWS ? n - r0 : CR_ROWS);
+        float tsq = 0.f;
+        if (act) {
+            for (int r = grp; r < rows; r += G) {
+                float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int q = 0; q < NA; ++q) stage_rows<float>(sa + q * CB_ROWS * K, a.p[q], r0, rows, CB_ROWS, K);
-        __syncthreads();
-        if (!act) continue;
-        for (int r = grp; r < rows; r += G) {
-            float s0 = 0.f, s1 = 0.f;
+                for (int q = 0; q < NA; ++q) {
+                    const float4 *ar = reinterpret_cast<const float4 *>(&sa[cur][q * CR_ROWS * K + r * K]);
 #pragma unroll
-            for (int q = 0; q < NA; ++q) {
-                const float4 *ar = reinterpret_cast<const float4 *>(sa + q * CB_ROWS * K + r * K);
-#pragma unroll
-                for (int c4 = 0; c4 < K / 4; ++c4) {
-                    const float4 v = ar[c4];
-                    const int c = q * K + 4 * c4;
-                    s0 = fmaf(v.x, c0[c], s0);
-                    s0 = fmaf(v.y, c0[c + 1], s0);
-                    s0 = fmaf(v.z, c0[c + 2], s0);
-                    s0 = fmaf(v.w, c0[c + 3], s0);
-                    if (q > 0) {
-                        s1 = fmaf(v.x, c1[c], s1);
-                        s1 = fmaf(v.y, c1[c + 1], s1);
-                        s1 = fmaf(v.z, c1[c + 2], s1);
-                        s1 = fmaf(v.w, c1[c + 3], s1);
+                    for (int c4 = 0; c4 < K / 4; ++c4) {
+                        const float4 v = ar[c4];
+                        const int c = q * K + 4 * c4;
+                        s0 = fmaf(v.x, c0[c], s0);
+                        s0 = fmaf(v.y, c0[c + 1], s0);
+                        s0 = fmaf(v.z, c0[c + 2], s0);
+                        s0 = fmaf(v.w, c0[c + 3], s0);
+                        if (q > 0) {
+                            s1 = fmaf(v.x, c1[c], s1);
+                            s1 = fmaf(v.y, c1[c + 1], s1);
+                            s1 = fmaf(v.z, c1[c + 2], s1);
+                            s1 = fmaf(v.w, c1[c + 3], s1);
+                        }
                     }
                 }
-            }
-            out.z[0][(r0 + r) * K + j] = s0;
-            if (out.norm_of == 0) nsq += static_cast<double>(s0) * s0;
-            if (nout > 1) {
-                out.z[1][(r0 + r) * K + j] = s1;
-                if (out.norm_of == 1) nsq += static_cast<double>(s1) * s1;
+                out.z[0][(r0 + r) * K + j] = s0;
+                if (out.norm_of == 0) tsq = fmaf(s0, s0, tsq);
+                if (nout > 1) {
+                    out.z[1][(r0 + r) * K + j] = s1;
+                    if (out.norm_of == 1) tsq = fmaf(s1, s1, tsq);
+                }
             }
         }
+        nsq += static_cast<double>(tsq);
+        __syncthreads();   // buffer `cur` is refilled next
+        cur ^= 1;
     }
     if (colsq) {
-        __syncthreads();
         if (act) atomicAdd(&red[j], nsq);
         __syncthreads();
         for (int q = threadIdx.x; q < K; q += blockDim.x) atomicAdd(&colsq[q], red[q]);
