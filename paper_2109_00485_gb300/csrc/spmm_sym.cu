@@ -66,7 +66,7 @@ struct __align__(16) WarpSmem {
 // narrow band of rows at any moment, so the X rows the band's tiles read and
 // the Y rows their transposed parts update stay in L2.
 #ifndef SPMM_GROUP
-#define SPMM_GROUP 2
+#define SPMM_GROUP 1
 #endif
 
 struct SpmmArgs {
@@ -148,7 +148,7 @@ __device__ __forceinline__ void load_a_tri(const float *v, int ks, int g, int t,
 
 // Issue the bulk copies of one chunk into stage s (one lane).
 template <int NT>
-__device__ __forceinline__ void issue_chunk(const SpmmArgs &a, WarpSmem<NT> *ws, int4 rec, int s, uint64_t pol_stream,
+__device__ __forceinline__ void issue_chunk(const SpmmArgs &a, int k, WarpSmem<NT> *ws, int4 rec, int s, uint64_t pol_stream,
                                             uint64_t pol_keep) {
     const int64_t off = static_cast<int64_t>((static_cast<uint64_t>(static_cast<uint32_t>(rec.y)) << 32) |
                                              static_cast<uint32_t>(rec.x));
@@ -156,18 +156,19 @@ __device__ __forceinline__ void issue_chunk(const SpmmArgs &a, WarpSmem<NT> *ws,
     const int npad = (info >> NPAD_SHIFT) & 0x3FF;
     const int64_t r0 = static_cast<int64_t>(ct) * TILE;
     const int rows = static_cast<int>(a.n - r0 < TILE ? a.n - r0 : TILE);
-    const uint32_t xbytes = static_cast<uint32_t>(rows) * a.k * 4u;
+    const uint32_t xbytes = static_cast<uint32_t>(rows) * k * 4u;
     ws->meta[s] = make_int4(ct, info, npad, rows);
     mbar_arrive_expect_tx(&ws->bar[s], static_cast<uint32_t>(npad) * 8u + xbytes);
     if (npad > 0) bulk_g2s(ws->cd[s], a.data + 2 * off, npad * 8u, &ws->bar[s], pol_stream);
-    bulk_g2s(ws->xt[s], a.X + r0 * a.k, xbytes, &ws->bar[s], pol_keep);
+    bulk_g2s(ws->xt[s], a.X + r0 * k, xbytes, &ws->bar[s], pol_keep);
 }
 
 __device__ __forceinline__ int4 load_rec(const ChunkRec *p, int64_t c) {
     return __ldg(reinterpret_cast<const int4 *>(p + c));
 }
 
-template <int NT>
+// KC: k as a compile-time constant (0: read from the arguments).
+template <int NT, int KC>
 __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_spmm_sym_tiled(SpmmArgs a) {
     using C = SpmmCfg<NT>;
     constexpr int S = C::STAGES;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<NT> *ws = reinterpret_cast<WarpSmem<NT> *>(smem_raw) + warp;
     const int g = lane >> 2, t = lane & 3;   // mma fragment coordinates
-    const int k = a.k;
+    const int k = KC > 0 ? KC : a.k;
 
     if (lane == 0) {
         for (int st = 0; st < S; ++st) mbar_init(&ws->bar[st], 1);
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         pend_ok = take_group();
         if (pend_ok) pending = load_rec(a.chunk, ic);
         for (int st = 0; st < S && pend_ok; ++st) {
-            issue_chunk<NT>(a, ws, pending, st, pol_stream, pol_keep);
+            issue_chunk<NT>(a, k, ws, pending, st, pol_stream, pol_keep);
             ++inflight;
             advance();
         }
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
             --inflight;
             if (pend_ok) {
                 fence_proxy_async();
-                issue_chunk<NT>(a, ws, pending, s, pol_stream, pol_keep);
+                issue_chunk<NT>(a, k, ws, pending, s, pol_stream, pol_keep);
                 ++inflight;
                 advance();
             }
@@ -497,14 +498,14 @@ __global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const
 
 // ---------------------------------------------------------------------------
 
-template <int NT>
+template <int NT, int KC>
 static cudaError_t launch_tiled(const lobpcg_ctx *h, const float *X, float *Y, int k, cudaStream_t s) {
     using C = SpmmCfg<NT>;
     const size_t smem = sizeof(WarpSmem<NT>) * C::WARPS;
     static bool attr_set[64] = {false};
     int dev = h->device;
     if (!attr_set[dev & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(k_spmm_sym_tiled<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_spmm_sym_tiled<NT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         attr_set[dev & 63] = true;
@@ -515,7 +516,7 @@ static cudaError_t launch_tiled(const lobpcg_ctx *h, const float *X, float *Y, i
     cudaError_t e = cudaMemsetAsync(h->T.sched, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     const int blocks = (h->T.warps + C::WARPS - 1) / C::WARPS;
-    k_spmm_sym_tiled<NT><<<blocks, C::WARPS * 32, smem, s>>>(a);
+    k_spmm_sym_tiled<NT, KC><<<blocks, C::WARPS * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -542,10 +543,17 @@ cudaError_t launch_spmm_sym_f32(const lobpcg_ctx *h, const float *X, float *Y, i
     if (e != cudaSuccess) return e;
     const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
     if (aligned && k % 4 == 0) {
-        if (k <= 8) return launch_tiled<1>(h, X, Y, k, s);
-        if (k <= 16) return launch_tiled<2>(h, X, Y, k, s);
-        if (k <= 24) return launch_tiled<3>(h, X, Y, k, s);
-        return launch_tiled<4>(h, X, Y, k, s);
+        switch (k) {   // the common block sizes with k known at compile time
+            case 8: return launch_tiled<1, 8>(h, X, Y, k, s);
+            case 16: return launch_tiled<2, 16>(h, X, Y, k, s);
+            case 20: return launch_tiled<3, 20>(h, X, Y, k, s);
+            case 32: return launch_tiled<4, 32>(h, X, Y, k, s);
+            default: break;
+        }
+        if (k <= 8) return launch_tiled<1, 0>(h, X, Y, k, s);
+        if (k <= 16) return launch_tiled<2, 0>(h, X, Y, k, s);
+        if (k <= 24) return launch_tiled<3, 0>(h, X, Y, k, s);
+        return launch_tiled<4, 0>(h, X, Y, k, s);
     }
     return launch_simple<float>(h, X, Y, k, s);
 }
