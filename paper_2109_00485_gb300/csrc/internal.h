@@ -24,8 +24,9 @@ constexpr int NPAD_SHIFT = 20;
 // Rows are grouped in row blocks of 16.  Within a row block the entries are
 // grouped by 16-column tile ("chunks"); the diagonal chunk comes first, then
 // the off-diagonal chunks in ascending tile order.  Inside a chunk entries
-// keep CSR order (by row, then column), so a chunk holding all 256 entries of
-// its tile is exactly that tile in row-major order.  Each chunk is padded to
+// keep CSR order (by row, then column), except in a chunk holding all 256
+// entries of its tile: that one is the tile row by row, with column c of a
+// row at position 4 (c mod 4) + c / 4 of the row.  Each chunk is padded to
 // a multiple of 4 entries (16 bytes) and stored as one contiguous run of
 // 2 npad words -- its npad index words, then its npad value words -- so one
 // bulk copy moves a whole chunk.

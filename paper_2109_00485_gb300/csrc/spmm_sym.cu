@@ -13,10 +13,12 @@
 //     Y_R += H_t X_C    (this row block's rows; accumulated over its chunks)
 //     Y_C  = H_t^T X_R  (the tile's column rows; added to Y by a bulk reduce)
 // Both are 16x16x16 products on the tensor cores (mma.sync m16n8k8, TF32).
-// FP32 accuracy comes from the 3-term split a = a_hi + a_lo (a_hi = tf32(a),
-// a_lo = tf32(a - a_hi)): a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
-// accumulation.  X_R (this row block's 16 rows of X) stays in registers as
-// split B fragments.  The diagonal chunk is expanded to S = L + L^T - D and
+// FP32 accuracy comes from the 3-term split a = a_hi + a_lo: a_hi is a with
+// its 13 low mantissa bits cleared (a TF32 value), a_lo = a - a_hi (exact in
+// FP32, |a_lo| < 2^-10 |a|), and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with
+// FP32 accumulation.  The tensor core reads a_lo as TF32 (its top 19 bits),
+// so each product carries a relative error below 3 * 2^-20.  X_R (this row
+// block's 16 rows of X) stays in registers as split B fragments.  The diagonal chunk is expanded to S = L + L^T - D and
 // applied as Y_R += S X_R.  Y_R of a row block is added to Y by a bulk
 // reduce too, since other warps add transposed parts to the same rows.
 #include <algorithm>
@@ -30,7 +32,7 @@ namespace lobpcg {
 // Pipeline depth and residency (tunable at build time; the row-block
 // partition made at create assumes SPMM_WARPS_PER_SM resident warps).
 #ifndef SPMM_STAGES
-#define SPMM_STAGES 3
+#define SPMM_STAGES 4
 #endif
 #ifndef SPMM_WARPS
 #define SPMM_WARPS 8
@@ -51,15 +53,18 @@ struct SpmmCfg {
     static constexpr int MINB = NT <= 2 ? SPMM_MINB : 1;
 };
 
+// Shared memory of one warp.  A partial chunk is scattered into the stage
+// it arrived in (its entries are first read into registers), so the
+// scattered tile needs no buffer of its own.
 template <int NT>
 struct __align__(16) WarpSmem {
     uint32_t cd[SpmmCfg<NT>::STAGES][512];        // one chunk: npad index words, then npad value words
     float xt[SpmmCfg<NT>::STAGES][TILE * 8 * NT];  // X rows of the chunk's column tile (row stride k)
-    float yt[2][TILE * 8 * NT];                     // Y tiles handed to the bulk reduce (double-buffered)
-    float H[TILE * HS];                             // scattered tile (or symmetric diagonal tile), row-major
+    float yt[TILE * 8 * NT];                        // Y tile handed to the bulk reduce
     int4 meta[SpmmCfg<NT>::STAGES];                 // column tile, info, padded count, valid rows
     uint64_t bar[SpmmCfg<NT>::STAGES];
 };
+static_assert(TILE * HS <= 512, "a scattered tile fits in one chunk stage");
 
 // Row blocks are handed out in order, SPMM_GROUP at a time, from a counter
 // in device memory (zeroed before each launch): all warps then work on a
@@ -82,14 +87,13 @@ struct SpmmArgs {
     int *err;
 };
 
-// Round to TF32 (10 stored mantissa bits), to nearest with ties away from
-// zero, by integer arithmetic on the bit pattern (two ALU operations).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-}
+// Split x = hi + lo for the 3-term product (two ALU operations): hi = x
+// with its 13 low mantissa bits cleared, lo = x - hi, exact in FP32.  lo is
+// handed to the tensor core as it is; the TF32 operand read ignores its low
+// 13 bits (a relative error below 2^-10 |lo| < 2^-20 |x|).
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 // d += a b  (m16n8k8, TF32 inputs, FP32 accumulate)
@@ -128,6 +132,32 @@ __device__ __forceinline__ void load_at(const float *T, int ks, int g, int t, ui
     split_tf32(p[8], ah[1], al[1]);
     split_tf32(p[4 * RS], ah[2], al[2]);
     split_tf32(p[4 * RS + 8], ah[3], al[3]);
+}
+
+// A full chunk stores column c of each row at position pc(c) = 4 (c mod 4) +
+// c / 4, so lane (g, t)'s four A-fragment columns t, t + 4, t + 8, t + 12 of
+// row g are one 16-byte word (both k-slices): two conflict-free vector loads.
+__device__ __forceinline__ void load_a_full(const float *v, int g, int t, uint32_t (&ah)[2][4], uint32_t (&al)[2][4]) {
+    const float4 r0 = *reinterpret_cast<const float4 *>(v + g * 16 + 4 * t);
+    const float4 r1 = *reinterpret_cast<const float4 *>(v + (g + 8) * 16 + 4 * t);
+    split_tf32(r0.x, ah[0][0], al[0][0]);
+    split_tf32(r1.x, ah[0][1], al[0][1]);
+    split_tf32(r0.y, ah[0][2], al[0][2]);
+    split_tf32(r1.y, ah[0][3], al[0][3]);
+    split_tf32(r0.z, ah[1][0], al[1][0]);
+    split_tf32(r1.z, ah[1][1], al[1][1]);
+    split_tf32(r0.w, ah[1][2], al[1][2]);
+    split_tf32(r1.w, ah[1][3], al[1][3]);
+}
+// The transposed fragment (slice ks) from a full chunk: T[8ks+t][g] sits at
+// row 8ks+t, position pc(g); column g + 8 two positions further on.
+__device__ __forceinline__ void load_at_full(const float *v, int ks, int g, int t, uint32_t (&ah)[4],
+                                             uint32_t (&al)[4]) {
+    const float *p = v + (8 * ks + t) * 16 + 4 * (g & 3) + (g >> 2);
+    split_tf32(p[0], ah[0], al[0]);
+    split_tf32(p[2], ah[1], al[1]);
+    split_tf32(p[64], ah[2], al[2]);
+    split_tf32(p[66], ah[3], al[3]);
 }
 
 // Offset of S[r][c] (S = L + L^T - D) in a complete diagonal chunk, whose
@@ -243,20 +273,39 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
     int64_t cur_rb = -1;
     int cur_rows = 0;
     uint32_t phases = 0;
-    int s = 0, yb = 0;
+    int s = 0;
 
     // Add a 16 x k tile from registers (D-fragment layout) to Y rows r0.. via
     // shared memory and one bulk reduce.
     auto reduce_tile = [&](const float (&d)[NT][4], int64_t r0, int rows) {
-        if (lane == 0) bulk_wait_read<1>();   // buffer yb was read by the reduce two tiles ago
+        if (lane == 0) bulk_wait_read<0>();   // the previous reduce has read the buffer
         __syncwarp();
-        float *yt = ws->yt[yb];
+        float *yt = ws->yt;
+        if (NT == 2 && KC == 16) {
+            // Lanes t and t^1 trade halves so that each holds four
+            // consecutive columns of one row: even t columns 2t..2t+3 (n-tile
+            // 0), odd t columns 8 + 2(t-1)..; one 16-byte store per row, the
+            // eight lanes of a store phase covering two whole rows.
+            const bool odd = t & 1;
+            const int c0 = odd ? 8 + 2 * (t - 1) : 2 * t;
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int col = 8 * nt + 2 * t;
-            if (col < k) {
-                *reinterpret_cast<float2 *>(yt + g * k + col) = make_float2(d[nt][0], d[nt][1]);
-                *reinterpret_cast<float2 *>(yt + (g + 8) * k + col) = make_float2(d[nt][2], d[nt][3]);
+            for (int h = 0; h < 2; ++h) {
+                const float s0 = odd ? d[0][2 * h] : d[NT - 1][2 * h];
+                const float s1 = odd ? d[0][2 * h + 1] : d[NT - 1][2 * h + 1];
+                const float r0v = __shfl_xor_sync(0xffffffffu, s0, 1);
+                const float r1v = __shfl_xor_sync(0xffffffffu, s1, 1);
+                const float4 v = odd ? make_float4(r0v, r1v, d[NT - 1][2 * h], d[NT - 1][2 * h + 1])
+                                     : make_float4(d[0][2 * h], d[0][2 * h + 1], r0v, r1v);
+                *reinterpret_cast<float4 *>(yt + (g + 8 * h) * 16 + c0) = v;
+            }
+        } else {
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int col = 8 * nt + 2 * t;
+                if (col < k) {
+                    *reinterpret_cast<float2 *>(yt + g * k + col) = make_float2(d[nt][0], d[nt][1]);
+                    *reinterpret_cast<float2 *>(yt + (g + 8) * k + col) = make_float2(d[nt][2], d[nt][3]);
+                }
             }
         }
         fence_proxy_async();
@@ -265,7 +314,6 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
             bulk_reduce_add_f32(a.Y + r0 * k, yt, static_cast<uint32_t>(rows * k) * 4u);
             bulk_commit();
         }
-        yb ^= 1;
     };
 
     while (true) {
@@ -292,24 +340,37 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         const float *sval = reinterpret_cast<const float *>(ws->cd[s] + m.z);
 
         // A chunk holding all 256 entries of its off-diagonal tile is that tile
-        // in row-major order (indices unique and sorted), and a diagonal chunk
+        // (rows in order, columns permuted as load_a_full reads them), and a diagonal chunk
         // holding all 136 entries of its lower triangle is that triangle in
         // row-major order, so their fragments are read straight from the
-        // staged values.  Any other chunk is scattered by its indices into a
-        // zeroed tile (a diagonal one into the symmetric S = L + L^T - D).
+        // staged values.  Any other chunk (fewer than 256 entries) is read
+        // into registers, then scattered by its indices into a zeroed tile
+        // (a diagonal one into the symmetric S = L + L^T - D) that takes the
+        // place of the chunk in its stage.
         const bool full = !is_diag && cnt == 256;
         const bool tri = is_diag && cnt == TILE * (TILE + 1) / 2;   // complete diagonal tile, canonical order
+        float *Hs = reinterpret_cast<float *>(ws->cd[s]);
         if (!full && !tri) {
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int e = lane; e < TILE * HS / 4; e += 32) reinterpret_cast<float4 *>(ws->H)[e] = z;
-            __syncwarp();
-            for (int e = lane; e < cnt; e += 32) {
-                const uint32_t u = sidx[e];
-                const float v = sval[e];
-                const int rl = (u >> 28) & 15, cl = u & 15;
-                ws->H[rl * HS + cl] = v;
-                if (is_diag) ws->H[cl * HS + rl] = v;
+            uint32_t eu[8];
+            float ev[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = lane + 32 * q;
+                eu[q] = (e < cnt) ? sidx[e] : IDX_PAD;
+                ev[q] = (e < cnt) ? sval[e] : 0.f;
             }
+            __syncwarp();
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = lane; e < TILE * HS / 4; e += 32) reinterpret_cast<float4 *>(Hs)[e] = z;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (eu[q] == IDX_PAD) continue;
+                const int rl = (eu[q] >> 28) & 15, cl = eu[q] & 15;
+                Hs[rl * HS + cl] = ev[q];
+                if (is_diag) Hs[cl * HS + rl] = ev[q];
+            }
+            fence_proxy_async();   // the stage is refilled by a bulk copy later
             __syncwarp();
         }
 
@@ -337,7 +398,7 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t ah[4], al[4];
                 if (tri) load_a_tri(sval, ks, g, t, ah, al);
-                else load_a<HS>(ws->H, ks, g, t, ah, al);
+                else load_a<HS>(Hs, ks, g, t, ah, al);
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
                     mma3(yr[nt], ah, al, xbh[ks][nt][0], xbh[ks][nt][1], xbl[ks][nt][0], xbl[ks][nt][1]);
@@ -351,15 +412,18 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) yc[nt][q] = yt4[nt][q] = 0.f;
+            uint32_t fah[2][4], fal[2][4];   // H_t fragments of both k-slices
+            if (full) load_a_full(sval, g, t, fah, fal);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 uint32_t ah[4], al[4], th[4], tl[4];
                 if (full) {
-                    load_a<16>(sval, ks, g, t, ah, al);    // H_t
-                    load_at<16>(sval, ks, g, t, th, tl);   // H_t^T
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { ah[q] = fah[ks][q]; al[q] = fal[ks][q]; }   // H_t
+                    load_at_full(sval, ks, g, t, th, tl);                                    // H_t^T
                 } else {
-                    load_a<HS>(ws->H, ks, g, t, ah, al);
-                    load_at<HS>(ws->H, ks, g, t, th, tl);
+                    load_a<HS>(Hs, ks, g, t, ah, al);
+                    load_at<HS>(Hs, ks, g, t, th, tl);
                 }
                 uint32_t bh[NT][2], bl[NT][2];
 #pragma unroll

@@ -93,9 +93,16 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
             if (FILL) {
                 uint32_t *ci = data + 2 * base, *cv = ci + tpad;
                 const int o = warp_excl_scan_i32(c_l);
+                // a full chunk (all 256 entries of its tile) keeps its rows in
+                // order, but stores column c of a row at position
+                // 4 (c mod 4) + c / 4, so that the four columns c, c + 4,
+                // c + 8, c + 12 one lane of the SpMM's tile products reads
+                // are one 16-byte word
+                const bool full = (tot == 256);
                 for (int t = 0; t < c_l; ++t) {
-                    ci[o + t] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
-                    cv[o + t] = __float_as_uint(static_cast<float>(val[p + t]));
+                    const int pos = full ? 4 * (t & 3) + (t >> 2) : t;
+                    ci[o + pos] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
+                    cv[o + pos] = __float_as_uint(static_cast<float>(val[p + t]));
                 }
                 if (lane < tpad - tot) { ci[tot + lane] = IDX_PAD; cv[tot + lane] = 0u; }
                 if (lane == 0) {

@@ -111,7 +111,9 @@ def test_diagonal_only():
     A = synth.CSR(n=n, row_ptr=np.arange(n + 1, dtype=np.int64), col=np.arange(n, dtype=np.int32), val=d)
     X, Y = run(A, 8)
     exact = d[:, None].astype(np.float64) * X
-    assert np.all(np.abs(Y - exact) <= 1e-6 * np.abs(exact))
+    # one product per output: the split product's error bound (3 * 2^-20
+    # relative) plus one float32 rounding, inside the 1e-5 SpMM tolerance
+    assert np.all(np.abs(Y - exact) <= 4e-6 * np.abs(exact))
 
 
 def test_long_row_over_4096_entries():
