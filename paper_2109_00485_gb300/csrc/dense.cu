@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(128) k_combine_reg(int64_t n, GemmBlocks<float
 
 // ---------------------------------------------------------------- small FP64 (one CTA)
 
-constexpr int EIG_MAXM_TRI = 96;
+
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -624,36 +624,109 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// GB300 issues one FP64 warp instruction per 64 cycles on each SM
+// sub-partition (one warp's dependent FP64 operations are 64 cycles apart,
+// and four warps on four sub-partitions reach the SM's FP64 rate), while an
+// FP64 division or square root is a sequence of several FP64 instructions.
+// The one-CTA kernels below therefore count FP64 warp instructions: lanes
+// are filled before warps are added, reciprocals and reciprocal square
+// roots start from a float32 estimate refined by Newton steps, and the
+// float32 estimate is taken from the bit pattern (integer operations only).
+
+// float32 value of x with its mantissa truncated (|x| within 2^+-100).
+__device__ __forceinline__ float f32_trunc(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = static_cast<unsigned>(((hi >> 20) & 0x7ff) - 1023 + 127);
+    const unsigned mant = (static_cast<unsigned>(hi & 0xfffff) << 3) | (lo >> 29);
+    return __uint_as_float((static_cast<unsigned>(hi) & 0x80000000u) | (e << 23) | mant);
+}
+// Exact float64 value of a normal float32 f.
+__device__ __forceinline__ double f64_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = ((u >> 23) & 0xffu) - 127u + 1023u;
+    const unsigned hi = (u & 0x80000000u) | (e << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>((u & 7u) << 29));
+}
+__device__ __forceinline__ bool in_seed_range(double x) {   // |x| within [2^-100, 2^100]
+    const int e = (__double2hiint(x) >> 20) & 0x7ff;
+    return e >= 1023 - 100 && e <= 1023 + 100;
+}
+// 1/q: float32 estimate (relative error ~2^-22), two Newton steps
+// r <- r + r (1 - q r); IEEE division outside the seed range.
+__device__ __forceinline__ double rcp64(double q) {
+    if (!in_seed_range(q)) return 1.0 / q;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(q)));
+    double r = f64_exact(rf);
+    double e = fma(-q, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-q, r, 1.0);
+    return fma(r, e, r);
+}
+// 1/sqrt(s) for s > 0: float32 estimate, two Newton steps r <- r (3/2 - s r^2 / 2).
+__device__ __forceinline__ double rsqrt64(double s) {
+    if (!in_seed_range(s)) return 1.0 / sqrt(s);
+    float rf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(s)));
+    double r = f64_exact(rf);
+    const double hs = 0.5 * s;
+    r = r * fma(-hs, r * r, 1.5);
+    return r * fma(-hs, r * r, 1.5);
+}
+// |a| >= |b| on the bit patterns (integer compare, no FP64 instruction).
+__device__ __forceinline__ bool abs_ge(double a, double b) {
+    return (static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7fffffffffffffffull) >=
+           (static_cast<unsigned long long>(__double_as_longlong(b)) & 0x7fffffffffffffffull);
+}
+
+// Row r and column c of the e-th entry of a strictly lower triangle listed
+// row by row ((1,0), (2,0), (2,1), ...): r(r-1)/2 <= e < r(r+1)/2.
+__device__ __forceinline__ void tri_rc(int e, int &r, int &c) {
+    int q = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) + 1.f) * 0.5f);
+    while (q * (q - 1) / 2 > e) --q;
+    while ((q + 1) * q / 2 <= e) ++q;
+    r = q;
+    c = e - q * (q - 1) / 2;
+}
+
 // In-place Cholesky of the m x m matrix A (lower triangle used), row-major in
-// shared memory.  Returns false if a pivot is not > 0 or the pivots span more
-// than `span` (max L_jj / min L_jj).
-__device__ bool cta_cholesky(double *A, int m, double span) {
+// shared memory: A = L L^T, L in the lower triangle, upper triangle zeroed.
+// Right-looking; the pivot reciprocal 1/L_jj goes to rd[j].  Returns false if
+// a pivot is not > 0 or the pivots span more than `span` (max L_jj / min L_jj).
+__device__ bool cta_cholesky(double *A, int m, double span, double *rd) {
     __shared__ int ok;
     __shared__ double dmin, dmax, rl;
     if (threadIdx.x == 0) { ok = 1; dmin = 1e300; dmax = 0.0; }
     __syncthreads();
-    // right-looking: after step j, column j holds L and the trailing block its Schur complement
     for (int j = 0; j < m; ++j) {
         if (threadIdx.x == 0) {
-            const double s = A[j * m + j];
-            if (!(s > 0.0)) {
+            const double sj = A[j * m + j];
+            if (!(sj > 0.0)) {
                 ok = 0;
             } else {
-                const double l = sqrt(s);
+                const double r = rsqrt64(sj);
+                const double l = sj * r;
                 A[j * m + j] = l;
-                rl = 1.0 / l;
+                rl = r;
+                rd[j] = r;
                 dmin = fmin(dmin, l);
                 dmax = fmax(dmax, l);
             }
         }
         __syncthreads();
         if (!ok) return false;
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= rl;
+        const double r = rl;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= r;
         __syncthreads();
+        // trailing lower triangle including its diagonal: pairs (i, l), j < l <= i
         const int nt = m - j - 1;
-        for (int q = threadIdx.x; q < nt * nt; q += blockDim.x) {
-            const int i = j + 1 + q / nt, l = j + 1 + q % nt;
-            if (l <= i) A[i * m + l] -= A[i * m + j] * A[l * m + j];
+        const int cnt = nt * (nt + 1) / 2;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            int r1, c1;
+            tri_rc(e, r1, c1);            // strictly lower pairs of an (nt + 1) triangle
+            const int i = j + r1, l = j + 1 + c1;
+            A[i * m + l] -= A[i * m + j] * A[l * m + j];
         }
         __syncthreads();
     }
@@ -665,20 +738,51 @@ __device__ bool cta_cholesky(double *A, int m, double span) {
     return dmax <= span * dmin;
 }
 
-// Li = L^{-1} for lower-triangular L (m x m, shared memory): column j by
-// forward substitution, one thread per column.
-__device__ void cta_tri_inverse(const double *L, double *Li, int m) {
-    __shared__ double rdiag[EIG_MAXM_TRI];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) rdiag[i] = 1.0 / L[i * m + i];
-    __syncthreads();
+// Li = L^{-1} for lower-triangular L (m x m, shared memory), rd[i] = 1/L_ii:
+// column j by forward substitution, one thread per column.
+__device__ void cta_tri_inverse(const double *L, const double *rd, double *Li, int m) {
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         for (int i = 0; i < m; ++i) {
             if (i < j) { Li[i * m + j] = 0.0; continue; }
             double s = (i == j) ? 1.0 : 0.0;
             for (int p = j; p < i; ++p) s -= L[i * m + p] * Li[p * m + j];
-            Li[i * m + j] = s * rdiag[i];
+            Li[i * m + j] = s * rd[i];
         }
     }
+    __syncthreads();
+}
+
+// B <- L^{-1} B for lower-triangular L (m x m) with rd[i] = 1 / L_ii; B is
+// m x nc, row stride nc (nc <= blockDim).  Right-looking: at step i row i
+// holds L_ii z_i (z = L^{-1} B), and rows below subtract L[r][i] z_i.  Rows
+// are scaled by rd at the end.  One barrier per step.
+__device__ void cta_trsm_rows(const double *L, const double *rd, double *B, int m, int nc) {
+    const int per = blockDim.x / nc;                 // rows per pass
+    const int c = threadIdx.x % nc, r0 = threadIdx.x / nc;
+    for (int i = 0; i + 1 < m; ++i) {
+        if (r0 < per) {
+            const double zi = B[i * nc + c] * rd[i];
+            for (int r = i + 1 + r0; r < m; r += per) B[r * nc + c] = fma(-L[r * m + i], zi, B[r * nc + c]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) B[e] *= rd[e / nc];
+    __syncthreads();
+}
+
+// Y <- L^{-T} Y (Y m x nc, row stride nc): back substitution, right-looking
+// from the last row, same conventions as cta_trsm_rows.
+__device__ void cta_trsm_rows_t(const double *L, const double *rd, double *Y, int m, int nc) {
+    const int per = blockDim.x / nc;
+    const int c = threadIdx.x % nc, r0 = threadIdx.x / nc;
+    for (int i = m - 1; i > 0; --i) {
+        if (r0 < per) {
+            const double ci = Y[i * nc + c] * rd[i];
+            for (int r = r0; r < i; r += per) Y[r * nc + c] = fma(-L[i * m + r], ci, Y[r * nc + c]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) Y[e] *= rd[e / nc];
     __syncthreads();
 }
 
@@ -790,77 +894,150 @@ __device__ int cta_jacobi(double *A, double *V, int m, double *cs, int *pairs, i
 }
 
 // The k smallest eigenpairs of the symmetric m x m matrix A (shared memory,
-// destroyed), FP64, one CTA (m <= 96, k <= 32):
+// lower triangle used, destroyed), FP64, one CTA of at least 128 threads
+// (m <= 96, k <= 32):
 //   1. Householder tridiagonalisation A = Q T Q^T (Golub & Van Loan,
-//      Section 8.3.1); the reflectors stay in A's lower triangle.
-//   2. Eigenvalue i of T by multisection on the Sturm count (the number of
-//      negative pivots of T - x I): float32 with 32 points per eigenvalue,
-//      then float64 with all k eigenvalues packed into one warp.
-//   3. Its eigenvector by inverse iteration: tridiagonal LU with partial
-//      pivoting of T - w_i I, three solves from distinct start vectors.
+//      Section 8.3.1), updating the lower triangle only; the reflectors stay
+//      in A's lower triangle.
+//   2. Eigenvalue brackets of T / ||T|| by float32 multisection on the Sturm
+//      count (the number of negative pivots of T - x I): one warp per
+//      eigenvalue, 32 points per step.
+//   3. float64 bisection of the brackets to 1e-10 ||T||: four warps (one per
+//      sub-partition), 128 / k points per eigenvalue, with the Sturm count as
+//      the sign changes of the leading principal minors p_r of T - x I
+//      (p_{r+1} = (d_r - x) p_r - e_{r-1}^2 p_{r-1}: no division).
+//   4. Eigenvector by two steps of inverse iteration with T - w_i I
+//      (tridiagonal LU with partial pivoting), one lane per pair, the pairs
+//      spread over four warps; the eigenvalue is then the Rayleigh quotient.
 //      Vectors of eigenvalues closer than 1e-10 ||T|| are re-orthogonalised.
-//   4. Back-transformation by the reflectors: V = Q Y.
+//   5. Back-transformation by the reflectors, V = Q Y, one warp per group of
+//      columns (no barrier between reflectors).
 // Outputs: w[0..k) ascending, V (m x k, row-major, shared memory).
 constexpr int EIG_MAXM = 96;
 
+// Step 5 of cta_eigh_smallest for one warp: columns c = warp + 4 cl of V,
+// rows r = rg + RG t (t < NR), lane = cl RG + rg.
+template <int NR>
+__device__ __forceinline__ void back_transform(const double *A, const double *tau, double *V, int m, int k, int warp,
+                                               int lane, int RG, int ncol) {
+    const int cl = lane / RG, rg = lane % RG;
+    const int c = warp + 4 * cl;
+    const bool colok = cl < ncol;
+    double vc[NR];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        const int r = rg + RG * t;
+        vc[t] = (colok && r < m) ? V[r * k + c] : 0.0;
+    }
+    for (int j = m - 3; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
+        double dot = 0.0;
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            const int r = rg + RG * t;
+            if (r > j && r < m) dot = fma(A[r * m + j], vc[t], dot);
+        }
+        for (int o = 1; o < RG; o <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        dot *= tj;
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            const int r = rg + RG * t;
+            if (r > j && r < m) vc[t] = fma(-dot, A[r * m + j], vc[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+        const int r = rg + RG * t;
+        if (colok && r < m) V[r * k + c] = vc[t];
+    }
+}
+
 __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V, double *d, double *e,
                                   double *tau, double *pv) {
-    __shared__ double red_s, tnorm;
-    __shared__ double blo[32], bhi[32], e2[EIG_MAXM];
+    __shared__ double red_s, tnorm, tau_s;
+    __shared__ double blo[32], bhi[32], e2[EIG_MAXM], sv[EIG_MAXM], sw[EIG_MAXM];
     __shared__ float df[EIG_MAXM], e2f[EIG_MAXM];
-    // 1. tridiagonalisation (reductions by warps, updates by all threads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    __shared__ double kk_s;
+    // 1. tridiagonalisation
     for (int j = 0; j + 2 < m; ++j) {
         if (warp == 0) {
             double sg = 0.0;
-            for (int i = j + 2 + lane; i < m; i += 32) sg += A[i * m + j] * A[i * m + j];
+            for (int i = j + 2 + lane; i < m; i += 32) sg = fma(A[i * m + j], A[i * m + j], sg);
             sg = warp_sum_d(sg);
             if (lane == 0) {
                 const double x0 = A[(j + 1) * m + j];
+                d[j] = A[j * m + j];
                 if (sg == 0.0) {
-                    tau[j] = 0.0;
+                    tau_s = 0.0;
                     e[j] = x0;
-                    red_s = 0.0;
                 } else {
-                    const double mu = sqrt(x0 * x0 + sg);
-                    const double alpha = (x0 <= 0.0) ? mu : -mu;   // reflect onto -sign(x0) ||x|| e_1
-                    const double v0 = x0 - alpha;
-                    tau[j] = 2.0 * v0 * v0 / (sg + v0 * v0);
-                    red_s = 1.0 / v0;
+                    // alpha = -sign(x0) mu, v = x - alpha e_1 scaled to v_0 = 1,
+                    // tau = 2 / (v^T v) = 1 + |x0| / mu, 1 / v_0 by Newton steps
+                    const double s2 = fma(x0, x0, sg);
+                    const double r = rsqrt64(s2);
+                    const double mu = s2 * r;
+                    const double alpha = (x0 <= 0.0) ? mu : -mu;
+                    tau_s = fma(fabs(x0), r, 1.0);
+                    red_s = rcp64(x0 - alpha);
                     e[j] = alpha;
                 }
-                A[(j + 1) * m + j] = 1.0;   // v_0 = 1
-                d[j] = A[j * m + j];
             }
         }
         __syncthreads();
-        const double tj = tau[j];
-        if (tj == 0.0) continue;
-        for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= red_s;
-        __syncthreads();
-        // p = tau A22 v: one warp per row
-        for (int i = j + 1 + warp; i < m; i += nwarps) {
-            double acc = 0.0;
-            for (int l = j + 1 + lane; l < m; l += 32) acc += A[i * m + l] * A[l * m + j];
-            acc = warp_sum_d(acc);
-            if (lane == 0) pv[i] = tj * acc;
+        const double tj = tau_s;
+        tau[j] = tj;   // every thread writes the same value
+        if (tj == 0.0) {
+            if (threadIdx.x == 0) A[(j + 1) * m + j] = 1.0;
+            __syncthreads();
+            continue;
+        }
+        const double rs = red_s;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+            const double v = (i == j + 1) ? 1.0 : A[i * m + j] * rs;
+            A[i * m + j] = v;
+            sv[i] = v;
         }
         __syncthreads();
+        // p = tau A22 v, four threads per row (A22 read through its lower triangle)
+        const int nt = m - j - 1;
+        const int qend = (4 * nt + 31) & ~31;   // whole warps, so the shuffles see every lane
+        for (int q = threadIdx.x; q < qend; q += blockDim.x) {
+            const bool act = q < 4 * nt;
+            const int i = j + 1 + (q >> 2), part = q & 3;
+            double a0 = 0.0, a1 = 0.0;
+            if (act) {
+                int l = j + 1 + part;
+                for (; l + 4 < m; l += 8) {
+                    const double m0 = (l <= i) ? A[i * m + l] : A[l * m + i];
+                    const double m1 = (l + 4 <= i) ? A[i * m + l + 4] : A[(l + 4) * m + i];
+                    a0 = fma(m0, sv[l], a0);
+                    a1 = fma(m1, sv[l + 4], a1);
+                }
+                if (l < m) a0 = fma((l <= i) ? A[i * m + l] : A[l * m + i], sv[l], a0);
+            }
+            double acc = a0 + a1;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (act && part == 0) pv[i] = tj * acc;
+        }
+        __syncthreads();
+        // K = tau v^T p / 2, w = p - K v
         if (warp == 0) {
             double kk = 0.0;
-            for (int l = j + 1 + lane; l < m; l += 32) kk += A[l * m + j] * pv[l];
+            for (int l = j + 1 + lane; l < m; l += 32) kk = fma(sv[l], pv[l], kk);
             kk = warp_sum_d(kk);
-            if (lane == 0) kk_s = 0.5 * tj * kk;
+            const double K = 0.5 * tj * kk;
+            for (int l = j + 1 + lane; l < m; l += 32) sw[l] = fma(-K, sv[l], pv[l]);
         }
         __syncthreads();
-        // A22 -= v w^T + w v^T with w = p - K v
-        const int mm = m - j - 1;
-        const double K = kk_s;
-        for (int q = threadIdx.x; q < mm * mm; q += blockDim.x) {
-            const int i = j + 1 + q / mm, l = j + 1 + q % mm;
-            const double vi = A[i * m + j], vl = A[l * m + j];
-            A[i * m + l] -= vi * (pv[l] - K * vl) + (pv[i] - K * vi) * vl;
+        // A22 -= v w^T + w v^T (lower triangle including the diagonal)
+        const int cnt = nt * (nt + 1) / 2;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            int r1, c1;
+            tri_rc(q, r1, c1);
+            const int i = j + r1, l = j + 1 + c1;
+            A[i * m + l] -= fma(sv[i], sw[l], sw[i] * sv[l]);
         }
         __syncthreads();
     }
@@ -876,23 +1053,28 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
             tn = fmax(tn, r);
         }
-        tnorm = tn;
+        tnorm = (tn > 0.0) ? tn : 1.0;
     }
+    __syncthreads();
+    // T / ||T||: diagonal d / ||T||, squared off-diagonal e^2 / ||T||^2
+    const double sc = rcp64(tnorm);
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
-        df[r] = static_cast<float>(d[r]);
+        const double ds = d[r] * sc;
+        d[r] = ds;
+        df[r] = static_cast<float>(ds);
         if (r + 1 < m) {
-            e2[r] = e[r] * e[r];
-            e2f[r] = static_cast<float>(e2[r]);
+            const double es = e[r] * sc;
+            e[r] = es;
+            e2[r] = es * es;
+            e2f[r] = static_cast<float>(es * es);
         }
     }
     __syncthreads();
-    // 2. eigenvalue estimates by float32 multisection: one warp per wanted
-    //    eigenvalue, its 32 lanes count the eigenvalues below 32 points of the
-    //    current bracket (Sturm count = negative pivots of T - x I), so each
-    //    step narrows the bracket 33-fold.  Float32 counts are exact away
-    //    from an eigenvalue by more than ~m eps32 ||T||.
+    // 2. float32 multisection: 32 points per step, each step narrows the
+    //    bracket 33-fold.  The float32 count is that of a matrix within a few
+    //    float32 roundings of T, so the bracket is widened by 4e-6.
     for (int i = warp; i < k; i += nwarps) {
-        float flo = static_cast<float>(-tnorm), fhi = static_cast<float>(tnorm);
+        float flo = -1.f, fhi = 1.f;
         for (int it = 0; it < 8 && fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f; ++it) {
             const float x = flo + (fhi - flo) * static_cast<float>(lane + 1) / 33.f;
             int cnt = 0;
@@ -903,57 +1085,62 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
                 q = (df[r] - x) - __fdividef(e2f[r - 1], q);
                 cnt += q < 0.f;
             }
-            // lanes whose point has more than i eigenvalues below it bound from above
             const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
-            const int first = above ? (__ffs(above) - 1) : 32;    // first lane with cnt > i
+            const int first = above ? (__ffs(above) - 1) : 32;    // first point with cnt > i
             const float nlo = (first == 0) ? flo : flo + (fhi - flo) * static_cast<float>(first) / 33.f;
             const float nhi = (first == 32) ? fhi : flo + (fhi - flo) * static_cast<float>(first + 1) / 33.f;
             flo = nlo;
             fhi = nhi;
         }
-        // the float32 bracket, widened by the float32 count uncertainty
         if (lane == 0) {
-            const double pad = 1e-5 * tnorm + 1e-300;
-            blo[i] = fmax(-tnorm, static_cast<double>(flo) - pad);
-            bhi[i] = fmin(tnorm, static_cast<double>(fhi) + pad);
+            blo[i] = fmax(-1.0 - 1e-5, static_cast<double>(flo) - 4e-6);
+            bhi[i] = fmin(1.0 + 1e-5, static_cast<double>(fhi) + 4e-6);
         }
     }
     __syncthreads();
-    // float64 multisection of all k brackets by warp 0 at once: eigenvalue
-    // i takes npts = 32 / k lanes, each counting below one interior point.
-    // (GB300 issues a float64 warp instruction over many cycles, so the
-    // float64 work is packed into as few warp instructions as possible.)
-    // The pivot reciprocal is a float32 seed refined by one Newton step
-    // (relative error ~1e-14, enough for the signs).
-    if (warp == 0) {
-        const int npts = 32 / k;
-        const int i = lane / npts, jp = lane % npts;
+    // 3. float64 bisection, warps 0..3: eigenvalue i on lanes [i npts, (i+1) npts)
+    //    of the 128, npts a power of two (so a group lies within one warp)
+    if (warp < 4) {
+        int npts = 32;
+        while (npts > 1 && npts * k > 128) npts >>= 1;
+        const int gl = warp * 32 + lane;
+        const int i = gl / npts, jp = gl % npts;
         const bool act = i < k;
+        const double frac = static_cast<double>(jp + 1) / static_cast<double>(npts + 1);
+        const double step = 1.0 / static_cast<double>(npts + 1);
         double lo = act ? blo[i] : 0.0, hi = act ? bhi[i] : 0.0;
-        for (int it = 0; it < 80; ++it) {
-            const bool done = !act || !(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300);
+        for (int it = 0; it < 40; ++it) {
+            const bool done = !act || !(hi - lo > 1e-10);
             if (__all_sync(0xffffffffu, done)) break;
-            const double x = lo + (hi - lo) * static_cast<double>(jp + 1) / static_cast<double>(npts + 1);
+            const double x = fma(hi - lo, frac, lo);
             int cnt = 0;
             if (act) {
-                double q = d[0] - x;
-                cnt += q < 0.0;
+                // a zero minor takes the sign opposite to the previous one (it
+                // counts as a sign change, as a zero pivot counts as negative)
+                double pp = 1.0, p = d[0] - x;
+                if ((__double_as_longlong(p) << 1) == 0) p = -0x1p-80;
+                cnt += __double2hiint(p) < 0;
                 for (int r = 1; r < m; ++r) {
-                    if (fabs(q) < 1e-280) q = (q < 0.0) ? -1e-280 : 1e-280;
-                    double rc = static_cast<double>(__frcp_rn(static_cast<float>(q)));
-                    if (!isfinite(rc)) rc = 1.0 / q;   // outside float range
-                    rc = rc * (2.0 - q * rc);
-                    q = (d[r] - x) - e2[r - 1] * rc;
-                    cnt += q < 0.0;
+                    const double t = e2[r - 1] * pp;
+                    double pn = fma(d[r] - x, p, -t);
+                    if ((__double_as_longlong(pn) << 1) == 0) pn = -p * 0x1p-80;
+                    cnt += (__double2hiint(pn) ^ __double2hiint(p)) < 0;
+                    pp = p;
+                    p = pn;
+                    if (((__double2hiint(p) >> 20) & 0x7ff) < 400) {   // |p| < 2^-623: rescale both (rare)
+                        p *= 0x1p+600;
+                        pp *= 0x1p+600;
+                    }
                 }
             }
             const unsigned above = __ballot_sync(0xffffffffu, act && cnt > i);
             if (act && !done) {
-                const unsigned grp = (above >> (i * npts)) & ((npts == 32) ? 0xffffffffu : ((1u << npts) - 1u));
+                const int sh = (i * npts) & 31;
+                const unsigned grp = (above >> sh) & ((npts == 32) ? 0xffffffffu : ((1u << npts) - 1u));
                 const int first = grp ? (__ffs(grp) - 1) : npts;   // first point with cnt > i
                 const double w0 = hi - lo;
-                const double nlo = (first == 0) ? lo : lo + w0 * static_cast<double>(first) / (npts + 1);
-                const double nhi = (first == npts) ? hi : lo + w0 * static_cast<double>(first + 1) / (npts + 1);
+                const double nlo = (first == 0) ? lo : fma(w0, step * first, lo);
+                const double nhi = (first == npts) ? hi : fma(w0, step * (first + 1), lo);
                 lo = nlo;
                 hi = nhi;
             }
@@ -961,115 +1148,120 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
         if (act && jp == 0) w[i] = 0.5 * (lo + hi);
     }
     __syncthreads();
-    // 3. eigenvector by inverse iteration in float64, one thread per pair;
-    //    the Ritz value is then the Rayleigh quotient y^T T y.
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const double tiny = 1e-300;
+    // 4. inverse iteration (T scaled by 1 / ||T||): pair i on warp i % 4, lane i / 4
+    if (warp < 4 && lane < (k + 3) / 4 && lane * 4 + warp < k) {
+        const int i = lane * 4 + warp;
         const double lam = w[i];
-        // inverse iteration: LU (partial pivoting) of T - lam I
-        double D[EIG_MAXM], DL[EIG_MAXM], DU[EIG_MAXM], DU2[EIG_MAXM], y[EIG_MAXM];
+        double D[EIG_MAXM], DL[EIG_MAXM], DU[EIG_MAXM], DU2[EIG_MAXM], rD[EIG_MAXM], y[EIG_MAXM];
         bool piv[EIG_MAXM];
-        const double pert = 2.2e-16 * tnorm + tiny;
+        const double pert = 0x1p-52;   // replaces an exactly zero pivot (T scaled to norm 1)
         for (int r = 0; r < m; ++r) {
             D[r] = d[r] - lam;
             DL[r] = (r + 1 < m) ? e[r] : 0.0;
-            DU[r] = (r + 1 < m) ? e[r] : 0.0;
+            DU[r] = DL[r];
             DU2[r] = 0.0;
-            piv[r] = false;
         }
         for (int r = 0; r + 1 < m; ++r) {
-            if (fabs(D[r]) >= fabs(DL[r])) {
-                if (D[r] == 0.0) D[r] = pert;
-                const double f = DL[r] / D[r];
+            const bool sw_ = !abs_ge(D[r], DL[r]);
+            piv[r] = sw_;
+            const double pvt = sw_ ? DL[r] : D[r];
+            const double rp = rcp64(pvt == 0.0 ? pert : pvt);
+            rD[r] = rp;
+            if (!sw_) {
+                const double f = DL[r] * rp;
                 DL[r] = f;
-                D[r + 1] -= f * DU[r];
+                D[r + 1] = fma(-f, DU[r], D[r + 1]);
             } else {
-                const double f = D[r] / DL[r];
-                D[r] = DL[r];
+                const double f = D[r] * rp;
+                D[r] = pvt;
                 DL[r] = f;
                 const double t = DU[r];
                 DU[r] = D[r + 1];
-                D[r + 1] = t - f * D[r + 1];
+                D[r + 1] = fma(-f, D[r + 1], t);
                 if (r + 2 < m) {
                     DU2[r] = DU[r + 1];
                     DU[r + 1] = -f * DU[r + 1];
                 }
-                piv[r] = true;
             }
         }
-        if (D[m - 1] == 0.0) D[m - 1] = pert;
-        for (int r = 0; r < m; ++r) D[r] = 1.0 / D[r];   // reciprocal pivots
-        for (int r = 0; r < m; ++r) y[r] = 1.0 + 0.25 * static_cast<double>((r * 7 + i * 13) % 11) / 11.0;
+        rD[m - 1] = rcp64(D[m - 1] == 0.0 ? pert : D[m - 1]);
+        // start vector 1 + (small multiples of 1/44), exact in float32
+        for (int r = 0; r < m; ++r) y[r] = f64_exact(1.f + 0.25f * static_cast<float>((r * 7 + i * 13) % 11) / 11.f);
         for (int sweep = 0; sweep < 2; ++sweep) {
             for (int r = 0; r + 1 < m; ++r) {
                 if (!piv[r]) {
-                    y[r + 1] -= DL[r] * y[r];
+                    y[r + 1] = fma(-DL[r], y[r], y[r + 1]);
                 } else {
                     const double t = y[r];
                     y[r] = y[r + 1];
-                    y[r + 1] = t - DL[r] * y[r];
+                    y[r + 1] = fma(-DL[r], y[r], t);
                 }
             }
-            y[m - 1] *= D[m - 1];
-            if (m >= 2) y[m - 2] = (y[m - 2] - DU[m - 2] * y[m - 1]) * D[m - 2];
-            for (int r = m - 3; r >= 0; --r) y[r] = (y[r] - DU[r] * y[r + 1] - DU2[r] * y[r + 2]) * D[r];
-            double nrm = 0.0;
-            for (int r = 0; r < m; ++r) nrm += y[r] * y[r];
-            nrm = 1.0 / sqrt(nrm);
-            for (int r = 0; r < m; ++r) y[r] *= nrm;
+            y[m - 1] *= rD[m - 1];
+            if (m >= 2) y[m - 2] = fma(-DU[m - 2], y[m - 1], y[m - 2]) * rD[m - 2];
+            for (int r = m - 3; r >= 0; --r) y[r] = fma(-DU2[r], y[r + 2], fma(-DU[r], y[r + 1], y[r])) * rD[r];
+            // no normalisation between the two solves: each grows y by at
+            // most 1 / (smallest pivot) <= 2^52, far inside the float64 range
         }
-        double rq = 0.0;
+        double n0 = 0.0, n1 = 0.0, q0 = 0.0, q1 = 0.0;
         for (int r = 0; r < m; ++r) {
             double ty = d[r] * y[r];
-            if (r > 0) ty += e[r - 1] * y[r - 1];
-            if (r + 1 < m) ty += e[r] * y[r + 1];
-            rq += y[r] * ty;
+            if (r > 0) ty = fma(e[r - 1], y[r - 1], ty);
+            if (r + 1 < m) ty = fma(e[r], y[r + 1], ty);
+            if (r & 1) { n1 = fma(y[r], y[r], n1); q1 = fma(y[r], ty, q1); }
+            else { n0 = fma(y[r], y[r], n0); q0 = fma(y[r], ty, q0); }
         }
-        w[i] = rq;
-        for (int r = 0; r < m; ++r) V[r * k + i] = y[r];
+        const double rn = rsqrt64(n0 + n1);
+        w[i] = (q0 + q1) * (rn * rn) * tnorm;   // Rayleigh quotient y^T T y / y^T y
+        for (int r = 0; r < m; ++r) V[r * k + i] = y[r] * rn;
     }
     __syncthreads();
     // re-orthogonalise vectors of (nearly) equal eigenvalues, in order
-    for (int i = 1; i < k; ++i) {
-        for (int j2 = 0; j2 < i; ++j2) {
-            if (fabs(w[i] - w[j2]) > 1e-10 * tnorm) continue;
-            if (threadIdx.x == 0) {
-                double dot = 0.0;
-                for (int r = 0; r < m; ++r) dot += V[r * k + i] * V[r * k + j2];
-                red_s = dot;
+    int close = 0;
+    for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+        const int i = q / k, j2 = q % k;
+        if (j2 < i) close |= fabs(w[i] - w[j2]) <= 1e-10 * tnorm;
+    }
+    if (__syncthreads_or(close)) {
+        for (int i = 1; i < k; ++i) {
+            for (int j2 = 0; j2 < i; ++j2) {
+                if (fabs(w[i] - w[j2]) > 1e-10 * tnorm) continue;
+                if (threadIdx.x == 0) {
+                    double dot = 0.0;
+                    for (int r = 0; r < m; ++r) dot += V[r * k + i] * V[r * k + j2];
+                    red_s = dot;
+                }
+                __syncthreads();
+                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] -= red_s * V[r * k + j2];
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double nrm = 0.0;
+                    for (int r = 0; r < m; ++r) nrm += V[r * k + i] * V[r * k + i];
+                    red_s = 1.0 / sqrt(nrm);
+                }
+                __syncthreads();
+                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] *= red_s;
+                __syncthreads();
             }
-            __syncthreads();
-            for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] -= red_s * V[r * k + j2];
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double nrm = 0.0;
-                for (int r = 0; r < m; ++r) nrm += V[r * k + i] * V[r * k + i];
-                red_s = 1.0 / sqrt(nrm);
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] *= red_s;
-            __syncthreads();
         }
     }
-    // 4. V = Q Y: apply the reflectors H_j = I - tau_j v_j v_j^T, last first
-    __shared__ double dots[32];
-    for (int j = m - 3; j >= 0; --j) {
-        const double tj = tau[j];
-        if (tj == 0.0) continue;
-        for (int c = warp; c < k; c += nwarps) {
-            double dot = 0.0;
-            for (int r = j + 1 + lane; r < m; r += 32) dot += A[r * m + j] * V[r * k + c];
-            dot = warp_sum_d(dot);
-            if (lane == 0) dots[c] = tj * dot;
-        }
-        __syncthreads();
-        const int rows = m - j - 1;
-        for (int q = threadIdx.x; q < rows * k; q += blockDim.x) {
-            const int r = j + 1 + q / k, c = q % k;
-            V[r * k + c] -= dots[c] * A[r * m + j];
-        }
-        __syncthreads();
+    // 5. V = Q Y: reflectors H_j = I - tau_j v_j v_j^T, last first.  Warps
+    //    0..3 (one per sub-partition) own columns c = warp + 4 u; a warp's
+    //    lanes are cpw column slots x RG row groups (row r in group r % RG),
+    //    so one FP64 instruction serves cpw columns and the reflectors need no
+    //    barrier between them.
+    if (warp < 4) {
+        const int ncol = (k - warp + 3) / 4;               // columns of this warp
+        int cpw = 1;
+        while (cpw < ncol) cpw <<= 1;                      // 1, 2, 4 or 8
+        const int RG = 32 / cpw;                           // row groups (>= 4)
+        const int rows = (m + RG - 1) / RG;                // rows per lane (<= 24)
+        if (rows <= 4) back_transform<4>(A, tau, V, m, k, warp, lane, RG, ncol);
+        else if (rows <= 8) back_transform<8>(A, tau, V, m, k, warp, lane, RG, ncol);
+        else if (rows <= 12) back_transform<12>(A, tau, V, m, k, warp, lane, RG, ncol);
+        else back_transform<24>(A, tau, V, m, k, warp, lane, RG, ncol);
     }
+    __syncthreads();
 }
 
 // Rayleigh-Ritz on the pencil (G, O) of eq. rreig: keep the k leftmost pairs.
@@ -1094,6 +1286,7 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
     __shared__ double tdd[EIG_MAXM], tee[EIG_MAXM], ttau[EIG_MAXM], tpv[EIG_MAXM];
     __shared__ int kept;
     __shared__ double red_big;
+    __shared__ double rdv[EIG_MAXM];
     int mm = m;
     int st = 0;
     bool chol = false;
@@ -1109,19 +1302,21 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
         __syncthreads();
     };
     load(mm);
-    chol = cta_cholesky(sO, mm, 1e4);
+    chol = cta_cholesky(sO, mm, 1e4, rdv);
     if (!chol && p0 < m) {
         mm = p0;
         st = 1;
         load(mm);
-        chol = cta_cholesky(sO, mm, 1e4);
+        chol = cta_cholesky(sO, mm, 1e4, rdv);
     }
     if (chol) {
-        // G_hat = L^{-1} G L^{-T}
-        cta_tri_inverse(sO, sV, mm);                   // sV = L^{-1}
-        cta_matmul(sV, false, sG, false, sO, mm);      // sO = L^{-1} G
-        cta_matmul(sO, false, sV, true, sG, mm);       // sG = L^{-1} G L^{-T}
-        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sO[e] = sV[e];   // keep L^{-1} in sO
+        // G_hat = L^{-1} G L^{-T} = L^{-1} (L^{-1} G)^T (G symmetric): two
+        // forward substitutions with a transpose between them; L stays in sO
+        cta_trsm_rows(sO, rdv, sG, mm, mm);           // sG = L^{-1} G
+        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sV[(e % mm) * mm + e / mm] = sG[e];
+        __syncthreads();
+        cta_trsm_rows(sO, rdv, sV, mm, mm);           // sV = L^{-1} G L^{-T}
+        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sG[e] = sV[e];
         __syncthreads();
     } else {
         // eigen route on the full pencil
@@ -1178,14 +1373,18 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
     __syncthreads();
     // k smallest eigenpairs of G_hat; eigenvectors (mm x k) into sV
     cta_eigh_smallest(sG, mm, k, wsort, sV, tdd, tee, ttau, tpv);
-    // C = B Y with B[i][p] = sO[p][i] (L^{-T}, or U s^{-1/2}); rows of a
-    // dropped P block are zero; undo the P scaling
-    const bool lower = chol;   // L^{-1} is lower triangular: B[i][p] = 0 for p < i
+    // C = L^{-T} Y (Cholesky route) or U s^{-1/2} Y (sO[p][i] = U[i][p]
+    // s_p^{-1/2}); rows of a dropped P block are zero; undo the P scaling
+    if (chol) cta_trsm_rows_t(sO, rdv, sV, mm, k);
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
         double sacc = 0.0;
         if (i < mm) {
-            for (int p = lower ? i : 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * k + j];
+            if (chol) {
+                sacc = sV[i * k + j];
+            } else {
+                for (int p = 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * k + j];
+            }
             if (pscale && i >= p0) sacc *= pscale[i - p0];
         }
         Cout[i * k + j] = sacc;
@@ -1201,13 +1400,13 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
 // s < 1e-12 s_max give zero columns.  W T has orthonormal (or zero) columns.
 // status[1] = 0 (Cholesky-QR) or 1 (SVQB).
 __global__ void k_orth_factor(int k, const double *B, double *Tout, int *status) {
-    __shared__ double sB[32 * 32], sL[32 * 32], dsc[32];
+    __shared__ double sB[32 * 32], sL[32 * 32], dsc[32], rdk[32];
     __shared__ double cs[2 * 16];
     __shared__ int pairs[2 * 16];
     __shared__ double smax;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const double b = B[j * k + j];
-        dsc[j] = (b > 0.0) ? 1.0 / sqrt(b) : 1.0;
+        dsc[j] = (b > 0.0) ? rsqrt64(b) : 1.0;
     }
     __syncthreads();
     auto load = [&]() {
@@ -1218,8 +1417,8 @@ __global__ void k_orth_factor(int k, const double *B, double *Tout, int *status)
         __syncthreads();
     };
     load();
-    if (cta_cholesky(sB, k, 1e7)) {
-        cta_tri_inverse(sB, sL, k);   // sL = L^{-1}
+    if (cta_cholesky(sB, k, 1e7, rdk)) {
+        cta_tri_inverse(sB, rdk, sL, k);   // sL = L^{-1}
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const int i = e / k, j = e % k;
             Tout[e] = dsc[i] * sL[j * k + i];

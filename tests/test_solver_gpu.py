@@ -161,3 +161,85 @@ def test_rayleigh_ritz_matches_library():
     assert np.all(np.abs(th - w) <= 1e-6 * np.abs(w).max())
     assert np.max(np.abs(C.T @ O @ C - np.eye(k))) <= 1e-5
     assert np.max(np.abs(G @ C - O @ C * th)) <= 1e-5 * np.abs(G).max()
+
+
+def _pencil_case(m, kind, seed):
+    """Float32 S, HS (n = m rows) whose Gram blocks are exactly G = S^T HS and
+    O = S^T S in float64: S = diag(2^-e) (powers of two), HS = diag(2^e) G."""
+    rng = np.random.default_rng(seed)
+    if kind == "clustered":
+        # the spectrum of a Ritz pencil: a few close eigenvalues below zero,
+        # the rest spread up to ||H|| ~ 200
+        lam = np.concatenate([[-0.8229, -0.8229 + 1e-6, -0.7129, -0.6859, -0.6858, -0.658],
+                              rng.uniform(-0.6, 200.0, m - 6)])[:m]
+        Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        G = (Q * lam) @ Q.T
+    elif kind == "repeated":
+        # two identical diagonal blocks: every eigenvalue exactly twice
+        h = m // 2
+        B = rng.standard_normal((h, h))
+        B = B + B.T
+        G = np.zeros((m, m))
+        G[:h, :h] = B
+        G[h:2 * h, h:2 * h] = B
+        if m % 2:
+            G[m - 1, m - 1] = 50.0
+    else:
+        B = rng.standard_normal((m, m))
+        G = B + B.T
+    # 14 significant bits: the Gram kernel's split products are then exact,
+    # so the GPU receives exactly G
+    G = np.tril(G.astype(np.float32)).view(np.uint32) & np.uint32(0xFFFFFE00)
+    G = G.view(np.float32)
+    G = G + np.tril(G, -1).T
+    top = 10 if kind == "illcond" else 3
+    e = rng.integers(0, top + 1, m)
+    if kind == "eigen_route":
+        e[1] = 15
+    s = np.exp2(-e.astype(np.float64)).astype(np.float32)
+    S = np.diag(s).astype(np.float32)
+    HS = (np.exp2(e.astype(np.float64))[:, None] * G).astype(np.float32)
+    Gx = S.astype(np.float64).T @ HS.astype(np.float64)
+    Ox = S.astype(np.float64).T @ S.astype(np.float64)
+    return S, HS, Gx, Ox
+
+
+@pytest.mark.parametrize("m,k,kind", [(5, 1, "random"), (24, 8, "clustered"), (47, 16, "random"),
+                                      (48, 16, "clustered"), (48, 16, "repeated"), (48, 16, "illcond"),
+                                      (60, 20, "clustered"), (96, 32, "random"), (48, 16, "eigen_route")])
+def test_rayleigh_ritz_pencils(m, k, kind):
+    """Rayleigh-Ritz on pencils known exactly in float64 (G with clustered or
+    exactly repeated eigenvalues, O = diag(4^-e) with pivot spans up to 2^3,
+    2^10, or 2^15 for the route through the eigendecomposition of O), against
+    the oracle's Cholesky + Jacobi solve (or, past the pivot span, the
+    standard problem O^-1/2 G O^-1/2).  A backward-stable solve in float64
+    determines every eigenvalue to a few eps64 ||O^-1/2 G O^-1/2||."""
+    import torch
+    pkg = _pkg()
+    S, HS, Gx, Ox = _pencil_case(m, kind, seed=m * 7 + k)
+    n = m
+    A = synth.CSR(n=n, row_ptr=np.arange(n + 1, dtype=np.int64), col=np.arange(n, dtype=np.int32),
+                  val=np.ones(n, dtype=np.float32))
+    h = pkg.from_csr(A, k=min(k, 32), nev=1)
+    C, th = h.rayleigh_ritz(torch.from_numpy(S).cuda(), torch.from_numpy(HS).cuda(), k)
+    C = C.cpu().numpy()
+    th = th.cpu().numpy()
+    h.destroy()
+    dsq = 1.0 / np.sqrt(np.diag(Ox))
+    lam_all = np.linalg.eigvalsh(dsq[:, None] * Gx * dsq[None, :])
+    if kind == "eigen_route":
+        # past the pivot span the pencil is solved in the eigenbasis of O,
+        # dropping directions with eigenvalue below 1e-8 of the largest
+        keep = np.diag(Ox) >= 1e-8 * np.diag(Ox).max()
+        lam_all = np.linalg.eigvalsh((dsq[:, None] * Gx * dsq[None, :])[np.ix_(keep, keep)])
+        lam = lam_all[:k]
+    else:
+        lam, _ = olb.rayleigh_ritz(Gx, Ox, k)
+    scale = np.abs(lam_all).max()
+    assert np.all(np.abs(th - lam) <= 1e-12 * m * scale), np.abs(th - lam).max() / scale
+    assert np.max(np.abs(C.T @ Ox @ C - np.eye(k))) <= 1e-9 * scale / np.abs(lam).max()
+    # residual of the pencil in the O^-1/2-scaled basis
+    resid = dsq[:, None] * (Gx @ C - Ox @ C * th)
+    if kind == "eigen_route":
+        resid = resid[keep]
+    assert np.max(np.abs(resid)) <= 1e-12 * m * scale * max(1.0, np.abs(C / dsq[:, None]).max())
