@@ -262,8 +262,8 @@ lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, 
     GemmBlocks<float> a{}, b{};
     a.p[0] = S;
     b.p[0] = HS;
-    e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream);
-    if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream);
+    e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream, h->d_err);
+    if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream, h->d_err);
     if (e == cudaSuccess) e = launch_rayleigh_ritz(m, k, m, G, O, m, nullptr, C, theta, status, h->stream);
     int hs = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);

@@ -19,6 +19,8 @@
 // iteration) or double (the FP64 refinement); Gram accumulation is FP64 for
 // both, small matrices are always FP64.
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 #include <cuda_runtime.h>
 #include "common.cuh"
@@ -263,14 +265,14 @@ __device__ __forceinline__ int gt_stride(int cols) {   // >= cols, = 24 (mod 32)
     return s;
 }
 
-// Round to TF32 (10 stored mantissa bits), to nearest with ties away from
-// zero, by integer arithmetic on the bit pattern (two ALU operations).
-__device__ __forceinline__ uint32_t gt_tf32(float x) {
-    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-}
+// Split x = hi + lo (two ALU operations): hi = x with its 13 low mantissa
+// bits cleared (a TF32 value), lo = x - hi, exact in FP32 and handed to the
+// tensor core as it is (the TF32 operand read ignores its low 13 bits, a
+// relative error below 2^-10 |lo| < 2^-20 |x|).  Each split product
+// a_hi b_hi + a_hi b_lo + a_lo b_hi then errs by less than 3 * 2^-20.
 __device__ __forceinline__ void gt_split(float x, uint32_t &hi, uint32_t &lo) {
-    hi = gt_tf32(x);
-    lo = gt_tf32(x - __uint_as_float(hi));
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void gt_mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                        uint32_t b0, uint32_t b1) {
@@ -1480,10 +1482,24 @@ cudaError_t launch_xupdate(int64_t n, int k, double *Z, const double *C, const f
     return cudaGetLastError();
 }
 
+// The tensor-memory Gram (gram_umma.cu) is chosen with LOBPCG_GRAM=umma; by
+// default float32 Grams use k_gram_tc, which is faster on these shapes.
+static bool gram_umma_enabled() {
+    static const int on = [] {
+        const char *v = getenv("LOBPCG_GRAM");
+        return (v && strcmp(v, "umma") == 0) ? 1 : 0;
+    }();
+    return on != 0;
+}
+
 template <typename T>
 cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmBlocks<T> b, double *M, int num_sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, int *err) {
     const int ma = na * k, mb = nb * k;
+    if constexpr (std::is_same<T, float>::value) {
+        if (err && gram_umma_enabled() && gram_umma_ok(k, na, a.p, nb, b.p))
+            return launch_gram_umma(n, k, na, a.p, nb, b.p, M, err, num_sms, s);
+    }
     cudaError_t e = cudaMemsetAsync(M, 0, sizeof(double) * ma * mb, s);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<T, float>::value) {
@@ -1599,9 +1615,9 @@ template cudaError_t launch_resid<float>(int64_t, int, const float *, const floa
 template cudaError_t launch_resid<double>(int64_t, int, const double *, const double *, const double *,
                                           const float *, double *, int, double *, int, cudaStream_t);
 template cudaError_t launch_gram<float>(int64_t, int, int, GemmBlocks<float>, int, GemmBlocks<float>, double *, int,
-                                        cudaStream_t);
+                                        cudaStream_t, int *);
 template cudaError_t launch_gram<double>(int64_t, int, int, GemmBlocks<double>, int, GemmBlocks<double>, double *,
-                                         int, cudaStream_t);
+                                         int, cudaStream_t, int *);
 template cudaError_t launch_combine<float>(int64_t, int, int, GemmBlocks<float>, int, CombineOut<float>, double *,
                                            int, cudaStream_t);
 template cudaError_t launch_combine<double>(int64_t, int, int, GemmBlocks<double>, int, CombineOut<double>,

@@ -34,9 +34,16 @@ cudaError_t launch_resid_mixed(int64_t n, int k, const double *X, const double *
                                cudaStream_t s);
 cudaError_t launch_xupdate(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
                            cudaStream_t s);
+// M (ma x mb, FP64) = A^T B.  With LOBPCG_GRAM=umma in the environment,
+// float32 blocks go to the tensor-memory kernel (gram_umma.cu) when it takes
+// the shape and err (device error word for its bounded waits) is given;
+// otherwise to the mma.sync kernel k_gram_tc.
 template <typename T>
 cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmBlocks<T> b, double *M, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, int *err = nullptr);
+bool gram_umma_ok(int k, int na, const float *const *ap, int nb, const float *const *bp);
+cudaError_t launch_gram_umma(int64_t n, int k, int na, const float *const *ap, int nb, const float *const *bp,
+                             double *M, int *err, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
                            int num_sms, cudaStream_t s);

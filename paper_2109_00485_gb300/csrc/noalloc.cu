@@ -84,8 +84,8 @@ extern "C" lobpcg_status lobpcg_rayleigh_ritz_noalloc(lobpcg_t h, const float *S
     b.p[0] = HS;
     // launch_gram clears its output before accumulating; the status word is
     // always written by the Rayleigh-Ritz kernel.
-    e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream);
-    if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream);
+    e = launch_gram<float>(h->T.n, m, 1, a, 1, b, G, h->num_sms, h->stream, h->d_err);
+    if (e == cudaSuccess) e = launch_gram<float>(h->T.n, m, 1, a, 1, a, O, h->num_sms, h->stream, h->d_err);
     if (e == cudaSuccess) e = launch_rayleigh_ritz(m, k, m, G, O, m, nullptr, C, theta, status, h->stream);
     int hs = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);

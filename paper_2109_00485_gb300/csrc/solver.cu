@@ -188,7 +188,7 @@ cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     GemmBlocks<T> ax{}, aw{};
     ax.p[0] = b.X;
     aw.p[0] = b.W;
-    CK(launch_gram<T>(n, k, 1, ax, 1, aw, s->B, h->num_sms, h->stream));          // B = X^T W
+    CK(launch_gram<T>(n, k, 1, ax, 1, aw, s->B, h->num_sms, h->stream, h->d_err));          // B = X^T W
     k_proj_coef<<<1, 256, 0, h->stream>>>(k, s->B, s->Cproj);
     CK(cudaGetLastError());
     GemmBlocks<T> awx{};
@@ -197,7 +197,7 @@ cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     CombineOut<T> o1{};
     o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1; o1.Cf = s->Cf;
     CK(launch_combine<T>(n, k, 2, awx, 1, o1, nullptr, h->num_sms, h->stream));   // W -= X B
-    CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream));          // B = W^T W
+    CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream, h->d_err));          // B = W^T W
     CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
     CombineOut<T> o2{};
     o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1; o2.Cf = s->Cf;
@@ -215,7 +215,7 @@ cudaError_t rr_on_x(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     GemmBlocks<T> ab{};
     ab.p[0] = b.HX;
     ab.p[1] = b.X;
-    CK(launch_gram<T>(n, k, 1, ax, 2, ab, s->G, h->num_sms, h->stream));   // [X^T HX | X^T X]
+    CK(launch_gram<T>(n, k, 1, ax, 2, ab, s->G, h->num_sms, h->stream, h->d_err));   // [X^T HX | X^T X]
     CK(launch_rayleigh_ritz(k, k, k, s->G, s->G + k, 2 * k, nullptr, s->C, s->theta, s->status, h->stream));
     CombineOut<T> ox{}, oh{};
     ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0; ox.norm_of = -1; ox.Cf = s->Cf;
@@ -268,7 +268,7 @@ cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool has
             aB.p[q] = aHS.p[q];
             aB.p[na + q] = aS.p[q];
         }
-        CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream));   // [S^T HS | S^T S]
+        CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));   // [S^T HS | S^T S]
         if (hasP) {
             k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
             CK(cudaGetLastError());
@@ -499,17 +499,17 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
             aB.p[q] = aHS.p[q];
             aB.p[na + q] = aS.p[q];
         }
-        CK(launch_gram<float>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream));
+        CK(launch_gram<float>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));
         GemmBlocks<double> ax{}, axx{};
         ax.p[0] = d.X;
         axx.p[0] = d.HX;
         axx.p[1] = d.X;
-        CK(launch_gram<double>(n, k, 1, ax, 2, axx, s->Gx, h->num_sms, h->stream));
+        CK(launch_gram<double>(n, k, 1, ax, 2, axx, s->Gx, h->num_sms, h->stream, h->d_err));
         GemmBlocks<float> ar{}, awp{};
         ar.p[0] = R32;
         awp.p[0] = f.W;
         awp.p[1] = f.P;
-        CK(launch_gram<float>(n, k, 1, ar, na - 1, awp, s->Rt, h->num_sms, h->stream));
+        CK(launch_gram<float>(n, k, 1, ar, na - 1, awp, s->Rt, h->num_sms, h->stream, h->d_err));
         k_patch_mixed<<<1, 256, 0, h->stream>>>(k, m, s->theta, s->Gx, s->Rt, s->G);
         CK(cudaGetLastError());
         if (hasP) {

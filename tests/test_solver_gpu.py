@@ -243,3 +243,42 @@ def test_rayleigh_ritz_pencils(m, k, kind):
     if kind == "eigen_route":
         resid = resid[keep]
     assert np.max(np.abs(resid)) <= 1e-12 * m * scale * max(1.0, np.abs(C / dsq[:, None]).max())
+
+
+def test_umma_gram_path_solve_matches_oracle():
+    """The tensor-memory Gram kernel (tcgen05.mma, chosen by LOBPCG_GRAM=umma)
+    in a full solve, run in a child process: eigenvalues and residuals against
+    the oracle as in test_solve_small_matches_oracle."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r"""
+import json, numpy as np, synth
+import paper_2109_00485_gb300 as pkg
+pkg.load()
+A = synth.tile_matrix(3000, 60, seed=4)
+A = synth.CSR(n=A.n, row_ptr=A.row_ptr, col=A.col, val=A.val.astype(np.float32))
+X0 = synth.initial_guess(A, 8, seed=1001, fp32=True)
+h = pkg.from_csr(A, k=8, nev=5, tol=1e-6, maxiter=1000, precond="diag", polish_fp64=1)
+X, ev, rs, st = h.solve(X0)
+X64 = h.get_x_f64().cpu().numpy()
+h.destroy()
+np.save("/tmp/umma_x64.npy", X64[:, :5])
+print(json.dumps({"ev": [float(v) for v in ev], "rs": [float(v) for v in rs], "conv": int(st["converged"])}))
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, LOBPCG_GRAM="umma", PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    A = f32_matrix(synth.tile_matrix(3000, 60, seed=4))
+    X0 = synth.initial_guess(A, 8, seed=1001, fp32=True)
+    ev = np.array(res["ev"])
+    assert res["conv"] == 1 and np.all(np.array(res["rs"]) <= 1e-6)
+    ref = olb.lobpcg(A, X0.astype(np.float64), 5, tol=1e-10, maxiter=2000, precond="diag")
+    normG = oracle.gershgorin(A)
+    assert np.all(eig_err(ev, ref.evals, normG) <= 1e-8), (ev, ref.evals)
+    rho = residuals_fp64(A, np.load("/tmp/umma_x64.npy"), ev)
+    assert np.all(rho <= 1.05e-6), rho
