@@ -80,7 +80,12 @@ typedef struct {
     int32_t precond;     /* 0 none, 1 diagonal, 2 block-Jacobi (64-row tiles), 3 learned MLP */
     int32_t resid_mode;  /* 0: ||r||/(max(|theta|,1e-12||H||_G)||x||), 1: ||r||/(||H||_G||x||) */
     int32_t polish_fp64; /* 1: finish with FP64 vectors once FP32 stagnates */
-    int32_t reserved;
+    int32_t tile_format; /* 0: every stored entry keeps its index word and value word (8 bytes,
+                            as CSR's column index and value); 1: a 16x16 tile holding all 256
+                            entries, or a diagonal tile with its complete lower triangle, keeps
+                            its value words only (4 bytes per entry, the positions implied;
+                            Section 3.3 keeps 2-byte local indices in its compressed sparse
+                            blocks for the same reason: fewer index bytes per entry) */
     uint64_t seed;
 } lobpcg_params;
 
@@ -109,6 +114,9 @@ typedef struct {
     double gershgorin;       /* ||H||_G = max_i sum_j |h_ij| over full rows */
     int32_t num_sms;
     int32_t warps;           /* warps the tiled SpMM kernel launches */
+    int32_t tile_format;     /* as created */
+    int32_t pad_;
+    int64_t stream_bytes;    /* bytes of the tiled entry stream one SpMM reads */
 } lobpcg_info;
 
 /*

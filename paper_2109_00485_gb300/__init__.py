@@ -42,7 +42,7 @@ class _Matrix(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("nev", ctypes.c_int32), ("maxiter", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("precond", ctypes.c_int32), ("resid_mode", ctypes.c_int32),
-                ("polish_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("polish_fp64", ctypes.c_int32), ("tile_format", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class _Stats(ctypes.Structure):
@@ -56,7 +56,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_blocks", ctypes.c_int64),
                 ("chunks", ctypes.c_int64), ("padded_nnz", ctypes.c_int64), ("full_chunks", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("gershgorin", ctypes.c_double), ("num_sms", ctypes.c_int32),
-                ("warps", ctypes.c_int32)]
+                ("warps", ctypes.c_int32), ("tile_format", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("stream_bytes", ctypes.c_int64)]
 
 
 def library_path() -> str:
@@ -371,7 +372,7 @@ def lobpcg_last_error() -> str:
 
 
 def make_params(k: int, nev: int | None = None, maxiter: int = 1000, tol: float = 1e-6, precond="diag",
-                resid_mode: int = 0, polish_fp64: int = 1, seed: int = 0) -> _Params:
+                resid_mode: int = 0, polish_fp64: int = 1, seed: int = 0, tile_format: int = 0) -> _Params:
     p = _Params()
     p.k = k
     p.nev = k if nev is None else nev
@@ -380,6 +381,7 @@ def make_params(k: int, nev: int | None = None, maxiter: int = 1000, tol: float 
     p.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
     p.resid_mode = resid_mode
     p.polish_fp64 = polish_fp64
+    p.tile_format = tile_format
     p.seed = seed & (2 ** 64 - 1)
     return p
 

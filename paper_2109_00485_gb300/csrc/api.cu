@@ -81,6 +81,7 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     const lobpcg_params &P = *params;
     if (P.k < 1 || P.k > 32) return fail(nullptr, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     if (P.nev < 1 || P.nev > P.k) return fail(nullptr, LOBPCG_ERR_ARG, "nev must be in [1, k]");
+    if (P.tile_format != 0 && P.tile_format != 1) return fail(nullptr, LOBPCG_ERR_ARG, "tile_format must be 0 or 1");
 
     lobpcg_ctx *h = new (std::nothrow) lobpcg_ctx();
     if (!h) return fail(nullptr, LOBPCG_ERR_OOM, "host allocation failed");
@@ -88,6 +89,7 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     h->stream = static_cast<cudaStream_t>(stream);
     h->T.n = A->n;
     h->T.nnz = A->nnz;
+    h->T.vonly = P.tile_format;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) {
@@ -175,6 +177,8 @@ lobpcg_status lobpcg_matrix_info(lobpcg_t h, lobpcg_info *info) {
     info->gershgorin = h->gershgorin;
     info->num_sms = h->num_sms;
     info->warps = h->T.warps;
+    info->tile_format = h->T.vonly;
+    info->stream_bytes = h->T.words * 4;
     return LOBPCG_OK;
 }
 

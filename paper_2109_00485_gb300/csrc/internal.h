@@ -18,6 +18,7 @@ struct __align__(16) ChunkRec {
     int32_t info;
 };
 constexpr int NPAD_SHIFT = 20;
+constexpr int VONLY_FLAG = 1 << 17;   // chunk info bit: value words only (a complete tile or diagonal triangle)
 
 // Tiled copy of the stored lower triangle.
 //
@@ -29,16 +30,21 @@ constexpr int NPAD_SHIFT = 20;
 // row at position 4 (c mod 4) + c / 4 of the row.  Each chunk is padded to
 // a multiple of 4 entries (16 bytes) and stored as one contiguous run of
 // 2 npad words -- its npad index words, then its npad value words -- so one
-// bulk copy moves a whole chunk.
+// bulk copy moves a whole chunk.  With tile_format 1 a chunk holding all
+// 256 entries of its tile, or the complete lower triangle (136 entries) of
+// a diagonal tile, keeps only its npad value words (VONLY_FLAG): the
+// positions of its entries are implied.
 //   index word = col | (row_in_block << 28), or IDX_PAD for padding
 //   value word = float32 bits (0 for padding)
-//   chunk[c].off   first (padded) entry of chunk c; its words start at
-//                  data[2 chunk[c].off]
+//   chunk[c].off   first word of chunk c in data[]
 //   chunk[c].ct    column tile of chunk c (col >> 4)
-//   chunk[c].info  real entry count | DIAG_FLAG (diagonal chunk) | npad << 20
+//   chunk[c].info  real entry count | DIAG_FLAG (diagonal chunk) |
+//                  VONLY_FLAG (value words only) | npad << 20
 //   rb_chunk[rb]   first chunk of row block rb (rb_chunk[R] = nchunks)
 struct Tiled {
     int64_t n = 0, nnz = 0, R = 0, nchunks = 0, npad = 0, full_chunks = 0;
+    int64_t words = 0;        // 32-bit words in data[]
+    int vonly = 0;            // tile_format 1: complete tiles store value words only
     uint32_t *data = nullptr;
     struct ChunkRec *chunk = nullptr;
     int64_t *rb_chunk = nullptr;

@@ -184,12 +184,14 @@ __device__ __forceinline__ void issue_chunk(const SpmmArgs &a, int k, WarpSmem<N
                                              static_cast<uint32_t>(rec.x));
     const int ct = rec.z, info = rec.w;
     const int npad = (info >> NPAD_SHIFT) & 0x3FF;
+    const bool vo = (info & VONLY_FLAG) != 0;    // value words only
     const int64_t r0 = static_cast<int64_t>(ct) * TILE;
     const int rows = static_cast<int>(a.n - r0 < TILE ? a.n - r0 : TILE);
     const uint32_t xbytes = static_cast<uint32_t>(rows) * k * 4u;
-    ws->meta[s] = make_int4(ct, info, npad, rows);
-    mbar_arrive_expect_tx(&ws->bar[s], static_cast<uint32_t>(npad) * 8u + xbytes);
-    if (npad > 0) bulk_g2s(ws->cd[s], a.data + 2 * off, npad * 8u, &ws->bar[s], pol_stream);
+    const uint32_t cbytes = static_cast<uint32_t>(npad) * (vo ? 4u : 8u);
+    ws->meta[s] = make_int4(ct, info, vo ? 0 : npad, rows);   // .z: first value word in the stage
+    mbar_arrive_expect_tx(&ws->bar[s], cbytes + xbytes);
+    if (npad > 0) bulk_g2s(ws->cd[s], a.data + off, cbytes, &ws->bar[s], pol_stream);
     bulk_g2s(ws->xt[s], a.X + r0 * k, xbytes, &ws->bar[s], pol_keep);
 }
 
@@ -508,8 +510,9 @@ __global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const
             const int64_t off = rec.off;
             const int info = rec.info;
             const int64_t npad = (info >> NPAD_SHIFT) & 0x3FF;
-            const uint32_t *cidx = data + 2 * off;
-            const uint32_t *cval = cidx + npad;
+            const bool vo = (info & VONLY_FLAG) != 0;
+            const uint32_t *cidx = data + off;
+            const uint32_t *cval = vo ? cidx : cidx + npad;
             const int cnt = info & 0xFFFF;
             const bool is_diag = (info & DIAG_FLAG) != 0;
             const int64_t ct = rec.ct;
@@ -517,9 +520,25 @@ __global__ void __launch_bounds__(256) k_spmm_sym_simple(int64_t n, int k, const
             for (int e = lane; e < TILE * 17; e += 32) ws->HT[e] = 0.f;
             __syncwarp();
             for (int e = lane; e < cnt; e += 32) {
-                const uint32_t u = cidx[e];
                 const float v = __uint_as_float(cval[e]);
-                const int rl = (u >> 28) & 15, cl = u & 15;
+                int rl, cl;
+                if (!vo) {
+                    const uint32_t u = cidx[e];
+                    rl = (u >> 28) & 15;
+                    cl = u & 15;
+                } else if (!is_diag) {
+                    // complete tile: row e / 16; position p within the row holds column 4 (p % 4) + p / 4
+                    const int p = e & 15;
+                    rl = e >> 4;
+                    cl = 4 * (p & 3) + (p >> 2);
+                } else {
+                    // complete lower triangle, row-major: row r holds entries r (r + 1) / 2 ..
+                    int r = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+                    while (r * (r + 1) / 2 > e) --r;
+                    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+                    rl = r;
+                    cl = e - r * (r + 1) / 2;
+                }
                 ws->H[rl * 16 + cl] = v;
                 if (is_diag) ws->H[cl * 16 + rl] = v;
                 else ws->HT[cl * 17 + rl] = v;

@@ -41,12 +41,15 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *row_ptr, const
 }
 
 // Warp per row block (lanes 0..15 own its rows).  COUNT pass: number of
-// chunks, padded entries and full chunks per row block.  FILL pass: writes
-// the entries and the chunk table at the offsets from the COUNT pass.
+// chunks, padded entries, data words and full chunks per row block.  FILL
+// pass: writes the entries and the chunk table at the offsets (chunks,
+// words) from the COUNT pass.  vonly: complete tiles and complete diagonal
+// triangles keep value words only.
 template <bool FILL, typename VT>
 __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const int32_t *col, const VT *val,
-                            int64_t *cnt_chunks, int64_t *cnt_npad, int64_t *cnt_full, const int64_t *rb_chunk,
-                            const int64_t *rb_nnz, uint32_t *data, ChunkRec *chunk) {
+                            int vonly, int64_t *cnt_chunks, int64_t *cnt_npad, int64_t *cnt_full,
+                            int64_t *cnt_words, const int64_t *rb_chunk, const int64_t *rb_words, uint32_t *data,
+                            ChunkRec *chunk) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t rb = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); rb < R;
@@ -61,24 +64,29 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
         const int dcnt = static_cast<int>(e - q);
         const int dtot = warp_sum_i32(dcnt);
         const int dpad = (dtot + 3) & ~3;
-        int64_t base = 0, cidx = 0, nch = 1, npad = dpad, nfull = 0;
+        const bool dvo = vonly && dtot == TILE * (TILE + 1) / 2;   // complete triangle (only in a full row block)
+        int64_t base = 0, cidx = 0, nch = 1, npad = dpad, nfull = 0, nwords = dvo ? dpad : 2 * dpad;
         if (FILL) {
-            base = rb_nnz[rb];
+            base = rb_words[rb];
             cidx = rb_chunk[rb];
-            // words [2 base, 2 base + dpad): indices; [2 base + dpad, 2 base + 2 dpad): values
-            uint32_t *ci = data + 2 * base, *cv = ci + dpad;
+            // words [base, base + dpad): indices (none when value-only); then dpad values
+            uint32_t *ci = data + base, *cv = dvo ? ci : ci + dpad;
             const int o = warp_excl_scan_i32(dcnt);
             for (int t = 0; t < dcnt; ++t) {
-                ci[o + t] = static_cast<uint32_t>(col[q + t]) | (static_cast<uint32_t>(lane) << 28);
+                if (!dvo) ci[o + t] = static_cast<uint32_t>(col[q + t]) | (static_cast<uint32_t>(lane) << 28);
                 cv[o + t] = __float_as_uint(static_cast<float>(val[q + t]));
             }
-            if (lane < dpad - dtot) { ci[dtot + lane] = IDX_PAD; cv[dtot + lane] = 0u; }
+            if (lane < dpad - dtot) {
+                if (!dvo) ci[dtot + lane] = IDX_PAD;
+                cv[dtot + lane] = 0u;
+            }
             if (lane == 0) {
                 ChunkRec r;
-                r.off = base; r.ct = static_cast<int32_t>(rb); r.info = dtot | DIAG_FLAG | (dpad << NPAD_SHIFT);
+                r.off = base; r.ct = static_cast<int32_t>(rb);
+                r.info = dtot | DIAG_FLAG | (dvo ? VONLY_FLAG : 0) | (dpad << NPAD_SHIFT);
                 chunk[cidx] = r;
             }
-            base += dpad;
+            base += dvo ? dpad : 2 * dpad;
             ++cidx;
         }
         // off-diagonal chunks: merge the 16 rows by column tile
@@ -90,8 +98,9 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
             while (p + c_l < q && (col[p + c_l] >> 4) == m) ++c_l;
             const int tot = warp_sum_i32(c_l);
             const int tpad = (tot + 3) & ~3;
+            const bool tvo = vonly && tot == 256;
             if (FILL) {
-                uint32_t *ci = data + 2 * base, *cv = ci + tpad;
+                uint32_t *ci = data + base, *cv = tvo ? ci : ci + tpad;
                 const int o = warp_excl_scan_i32(c_l);
                 // a full chunk (all 256 entries of its tile) keeps its rows in
                 // order, but stores column c of a row at position
@@ -101,25 +110,31 @@ __global__ void k_tile_rows(int64_t n, int64_t R, const int64_t *row_ptr, const 
                 const bool full = (tot == 256);
                 for (int t = 0; t < c_l; ++t) {
                     const int pos = full ? 4 * (t & 3) + (t >> 2) : t;
-                    ci[o + pos] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
+                    if (!tvo) ci[o + pos] = static_cast<uint32_t>(col[p + t]) | (static_cast<uint32_t>(lane) << 28);
                     cv[o + pos] = __float_as_uint(static_cast<float>(val[p + t]));
                 }
                 if (lane < tpad - tot) { ci[tot + lane] = IDX_PAD; cv[tot + lane] = 0u; }
                 if (lane == 0) {
                     ChunkRec r;
-                    r.off = base; r.ct = m; r.info = tot | (tpad << NPAD_SHIFT);
+                    r.off = base; r.ct = m; r.info = tot | (tvo ? VONLY_FLAG : 0) | (tpad << NPAD_SHIFT);
                     chunk[cidx] = r;
                 }
-                base += tpad;
+                base += tvo ? tpad : 2 * tpad;
                 ++cidx;
             } else {
                 ++nch;
                 npad += tpad;
+                nwords += tvo ? tpad : 2 * tpad;
                 nfull += (tot == 256);
             }
             p += c_l;
         }
-        if (!FILL && lane == 0) { cnt_chunks[rb] = nch; cnt_npad[rb] = npad; cnt_full[rb] = nfull; }
+        if (!FILL && lane == 0) {
+            cnt_chunks[rb] = nch;
+            cnt_npad[rb] = npad;
+            cnt_full[rb] = nfull;
+            cnt_words[rb] = nwords;
+        }
     }
 }
 
@@ -200,38 +215,42 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
 
     // 2. count chunks per row block
     int64_t *d_cnt = nullptr;
-    TRY(cudaMallocAsync(&d_cnt, sizeof(int64_t) * 3 * R, s));
+    TRY(cudaMallocAsync(&d_cnt, sizeof(int64_t) * 4 * R, s));
     const int wpb = 8;
     const int64_t tblocks = std::min<int64_t>((R + wpb - 1) / wpb, 65535LL * 16);
     k_tile_rows<false, VT><<<static_cast<unsigned>(tblocks), wpb * 32, 0, s>>>(
-        n, R, row_ptr, col, val, d_cnt, d_cnt + R, d_cnt + 2 * R, nullptr, nullptr, nullptr, nullptr);
+        n, R, row_ptr, col, val, T.vonly, d_cnt, d_cnt + R, d_cnt + 2 * R, d_cnt + 3 * R, nullptr, nullptr,
+        nullptr, nullptr);
     TRY(cudaGetLastError());
-    std::vector<int64_t> cnt(3 * R);
-    TRY(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * 3 * R, cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> cnt(4 * R);
+    TRY(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * 4 * R, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
-    std::vector<int64_t> rb_chunk(R + 1), rb_nnz(R + 1);
-    rb_chunk[0] = rb_nnz[0] = 0;
-    int64_t full = 0;
+    std::vector<int64_t> rb_chunk(R + 1), rb_words(R + 1);
+    rb_chunk[0] = rb_words[0] = 0;
+    int64_t full = 0, npad = 0;
     for (int64_t r = 0; r < R; ++r) {
         rb_chunk[r + 1] = rb_chunk[r] + cnt[r];
-        rb_nnz[r + 1] = rb_nnz[r] + cnt[R + r];
+        rb_words[r + 1] = rb_words[r] + cnt[3 * R + r];
+        npad += cnt[R + r];
         full += cnt[2 * R + r];
     }
     T.nchunks = rb_chunk[R];
-    T.npad = rb_nnz[R];
+    T.npad = npad;
+    T.words = rb_words[R];
     T.full_chunks = full;
 
     // 3. allocate the tiled arrays and fill them
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.data), sizeof(uint32_t) * 2 * std::max<int64_t>(T.npad, 4)));
+    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.data), sizeof(uint32_t) * std::max<int64_t>(T.words, 8)));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk), sizeof(ChunkRec) * T.nchunks));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.rb_chunk), sizeof(int64_t) * (R + 1)));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.diag), sizeof(float) * n));
-    int64_t *d_rb_nnz = nullptr;
-    TRY(cudaMallocAsync(&d_rb_nnz, sizeof(int64_t) * (R + 1), s));
+    int64_t *d_rb_words = nullptr;
+    TRY(cudaMallocAsync(&d_rb_words, sizeof(int64_t) * (R + 1), s));
     TRY(cudaMemcpyAsync(T.rb_chunk, rb_chunk.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(d_rb_nnz, rb_nnz.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(d_rb_words, rb_words.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
     k_tile_rows<true, VT><<<static_cast<unsigned>(tblocks), wpb * 32, 0, s>>>(
-        n, R, row_ptr, col, val, nullptr, nullptr, nullptr, T.rb_chunk, d_rb_nnz, T.data, T.chunk);
+        n, R, row_ptr, col, val, T.vonly, nullptr, nullptr, nullptr, nullptr, T.rb_chunk, d_rb_words, T.data,
+        T.chunk);
     TRY(cudaGetLastError());
     k_diag<VT><<<static_cast<unsigned>(gblocks), tpb, 0, s>>>(n, row_ptr, col, val, T.diag);
     TRY(cudaGetLastError());
@@ -259,7 +278,7 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.sched), sizeof(int) * 4));
 
     TRY(cudaFreeAsync(d_rowsum, s));
-    TRY(cudaFreeAsync(d_rb_nnz, s));
+    TRY(cudaFreeAsync(d_rb_words, s));
     TRY(cudaFreeAsync(d_cnt, s));
     TRY(cudaFreeAsync(d_bad, s));
     TRY(cudaStreamSynchronize(s));

@@ -282,3 +282,20 @@ print(json.dumps({"ev": [float(v) for v in ev], "rs": [float(v) for v in rs], "c
     assert np.all(eig_err(ev, ref.evals, normG) <= 1e-8), (ev, ref.evals)
     rho = residuals_fp64(A, np.load("/tmp/umma_x64.npy"), ev)
     assert np.all(rho <= 1.05e-6), rho
+
+
+def test_solve_value_only_tiles_matches_oracle():
+    """The solve with tile_format 1 (value-only complete tiles): eigenvalues
+    and residuals against the oracle as in test_solve_small_matches_oracle."""
+    pkg = _pkg()
+    A = f32_matrix(synth.tile_matrix(3000, 60, seed=4))
+    X0 = synth.initial_guess(A, 8, seed=1001, fp32=True)
+    h = pkg.from_csr(A, k=8, nev=5, tol=1e-6, maxiter=1000, precond="diag", polish_fp64=1, tile_format=1)
+    X, ev, rs, st = h.solve(X0)
+    X64 = h.get_x_f64().cpu().numpy()
+    h.destroy()
+    assert st["converged"] == 1 and np.all(rs <= 1e-6)
+    ref = olb.lobpcg(A, X0.astype(np.float64), 5, tol=1e-10, maxiter=2000, precond="diag")
+    normG = oracle.gershgorin(A)
+    assert np.all(eig_err(ev, ref.evals, normG) <= 1e-8), (ev, ref.evals)
+    assert np.all(residuals_fp64(A, X64[:, :5], ev) <= 1.05e-6)

@@ -232,3 +232,55 @@ def test_full_size_n2m_sampled_rows():
     b = (torch.from_numpy(X1).cuda().double().T @ Y2.double()).cpu().numpy()
     assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(a))
     h.destroy()
+
+
+def _mixed_tiles(n, seed):
+    """Lower triangle with complete 16x16 tiles, complete diagonal tiles,
+    partial tiles and a partial last row block (n not a multiple of 16)."""
+    A = synth.tile_matrix(n, 60, seed=seed, fp32=True)
+    rng = np.random.default_rng(seed)
+    keep = rng.random(A.nnz) < 0.97                 # punch holes into some tiles
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    keep |= rows == A.col                           # keep the diagonal
+    # keep every tile of the first 40 row blocks complete
+    keep |= rows < 640
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, rows[keep] + 1, 1)
+    return synth.CSR(n=n, row_ptr=np.cumsum(rp), col=A.col[keep], val=A.val[keep])
+
+
+@pytest.mark.parametrize("k", [8, 16, 20, 32, 7, 12])
+def test_value_only_tiles_match_oracle(k):
+    """tile_format 1 (complete tiles and complete diagonal triangles keep
+    value words only): tiled kernel (k % 4 == 0) and simple kernel (other k)
+    against the oracle, and bit-for-bit equal to tile_format 0 on the
+    simple kernel's float64 path."""
+    import torch
+    A = _mixed_tiles(3001, seed=31)
+    X, Y = run(A, k, tile_format=1)
+    check(A, X, Y)
+    pkg = _pkg()
+    h = pkg.from_csr(A, k=min(k, 32), nev=1, tile_format=1)
+    info = h.info()
+    assert info["tile_format"] == 1 and info["full_chunks"] > 0
+    Xd = torch.from_numpy(X.astype(np.float64)).cuda()
+    Y64 = h.spmm_sym_f64(Xd).cpu().numpy()
+    h.destroy()
+    h0 = pkg.from_csr(A, k=min(k, 32), nev=1)
+    Y64b = h0.spmm_sym_f64(Xd).cpu().numpy()
+    info0 = h0.info()
+    h0.destroy()
+    Yo = oracle.spmm_tri(A, X.astype(np.float64))
+    scale = oracle.spmm_tri(abs_csr(A), np.abs(X.astype(np.float64)))
+    assert np.all(np.abs(Y64 - Yo) <= 1e-12 * scale + 1e-300)
+    assert np.all(np.abs(Y64b - Yo) <= 1e-12 * scale + 1e-300)
+    # value-only storage: every complete tile saves its 256 index words
+    assert info["stream_bytes"] < info0["stream_bytes"] - 4 * 256 * info["full_chunks"] + 1
+
+
+def test_value_only_full_workload_rows_sampled():
+    """tile_format 1 on a 400-per-row matrix (every off-diagonal tile complete),
+    n = 200,016, k = 16: all rows against the oracle."""
+    A = synth.tile_matrix(200016, 400, seed=2, fp32=True)
+    X, Y = run(A, 16, tile_format=1)
+    check(A, X, Y)
