@@ -11,16 +11,18 @@
 // columns select.  The warp scatters the entries into the dense 16x16 tile
 // H_t and its transpose (zero-filled when the chunk is partial), then
 //     Y_R += H_t X_C    (this row block's rows; accumulated over its chunks)
-//     Y_C  = H_t^T X_R  (the tile's column rows; added to Y by a bulk reduce)
+//     Y_C  = H_t^T X_R  (the tile's column rows, added to Y by 16-byte
+//                        vector reductions in L2)
 // Both are 16x16x16 products on the tensor cores (mma.sync m16n8k8, TF32).
 // FP32 accuracy comes from the 3-term split a = a_hi + a_lo: a_hi is a with
 // its 13 low mantissa bits cleared (a TF32 value), a_lo = a - a_hi (exact in
 // FP32, |a_lo| < 2^-10 |a|), and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with
 // FP32 accumulation.  The tensor core reads a_lo as TF32 (its top 19 bits),
 // so each product carries a relative error below 3 * 2^-20.  X_R (this row
-// block's 16 rows of X) stays in registers as split B fragments.  The diagonal chunk is expanded to S = L + L^T - D and
-// applied as Y_R += S X_R.  Y_R of a row block is added to Y by a bulk
-// reduce too, since other warps add transposed parts to the same rows.
+// block's 16 rows of X) stays in registers as split B fragments.  The
+// diagonal chunk is expanded to S = L + L^T - D and applied as
+// Y_R += S X_R.  Y_R of a row block is added to Y by vector reductions too,
+// since other warps add transposed parts to the same rows.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -60,9 +62,8 @@ template <int NT>
 struct __align__(16) WarpSmem {
     uint32_t cd[SpmmCfg<NT>::STAGES][512];        // one chunk: npad index words, then npad value words
     float xt[SpmmCfg<NT>::STAGES][TILE * 8 * NT];  // X rows of the chunk's column tile (row stride k)
-    float yt[TILE * 8 * NT];                        // Y tile handed to the bulk reduce
     int4 meta[SpmmCfg<NT>::STAGES];                 // column tile, info, padded count, valid rows
-    uint64_t bar[SpmmCfg<NT>::STAGES];
+    uint64_t bar[SpmmCfg<NT>::STAGES];              // stage filled (bulk-copy bytes landed)
 };
 static_assert(TILE * HS <= 512, "a scattered tile fits in one chunk stage");
 
@@ -277,44 +278,41 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
     uint32_t phases = 0;
     int s = 0;
 
-    // Add a 16 x k tile from registers (D-fragment layout) to Y rows r0.. via
-    // shared memory and one bulk reduce.
+    // Add a 16 x k tile from registers (D-fragment layout) to Y rows r0..
+    // r0 + rows - 1 with 16-byte vector reductions in L2 (red.global.add.v4):
+    // lanes t and t^1 trade halves so that each holds four consecutive
+    // columns of one row.  For a pair of n-tiles (2p, 2p+1) an even lane
+    // takes row g of tile 2p and an odd lane row g of tile 2p+1 (then rows
+    // g + 8); a last unpaired n-tile goes to even lanes for row g and odd
+    // lanes for row g + 8.  (A bulk reduce per tile is one more operation
+    // for the SM's TMA unit, whose operations bound this kernel.)
     auto reduce_tile = [&](const float (&d)[NT][4], int64_t r0, int rows) {
-        if (lane == 0) bulk_wait_read<0>();   // the previous reduce has read the buffer
-        __syncwarp();
-        float *yt = ws->yt;
-        if (NT == 2 && KC == 16) {
-            // Lanes t and t^1 trade halves so that each holds four
-            // consecutive columns of one row: even t columns 2t..2t+3 (n-tile
-            // 0), odd t columns 8 + 2(t-1)..; one 16-byte store per row, the
-            // eight lanes of a store phase covering two whole rows.
-            const bool odd = t & 1;
-            const int c0 = odd ? 8 + 2 * (t - 1) : 2 * t;
+        const bool odd = t & 1;
+#pragma unroll
+        for (int pq = 0; pq + 1 < NT; pq += 2) {
+            const int c0 = odd ? 8 * (pq + 1) + 2 * (t - 1) : 8 * pq + 2 * t;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float s0 = odd ? d[0][2 * h] : d[NT - 1][2 * h];
-                const float s1 = odd ? d[0][2 * h + 1] : d[NT - 1][2 * h + 1];
-                const float r0v = __shfl_xor_sync(0xffffffffu, s0, 1);
-                const float r1v = __shfl_xor_sync(0xffffffffu, s1, 1);
-                const float4 v = odd ? make_float4(r0v, r1v, d[NT - 1][2 * h], d[NT - 1][2 * h + 1])
-                                     : make_float4(d[0][2 * h], d[0][2 * h + 1], r0v, r1v);
-                *reinterpret_cast<float4 *>(yt + (g + 8 * h) * 16 + c0) = v;
-            }
-        } else {
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int col = 8 * nt + 2 * t;
-                if (col < k) {
-                    *reinterpret_cast<float2 *>(yt + g * k + col) = make_float2(d[nt][0], d[nt][1]);
-                    *reinterpret_cast<float2 *>(yt + (g + 8) * k + col) = make_float2(d[nt][2], d[nt][3]);
-                }
+                const float s0 = odd ? d[pq][2 * h] : d[pq + 1][2 * h];
+                const float s1 = odd ? d[pq][2 * h + 1] : d[pq + 1][2 * h + 1];
+                const float v0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+                const float v1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                const int row = g + 8 * h;
+                const float4 v = odd ? make_float4(v0, v1, d[pq + 1][2 * h], d[pq + 1][2 * h + 1])
+                                     : make_float4(d[pq][2 * h], d[pq][2 * h + 1], v0, v1);
+                if (row < rows && c0 + 4 <= k) red_add_v4(a.Y + (r0 + row) * k + c0, v.x, v.y, v.z, v.w);
             }
         }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) {
-            bulk_reduce_add_f32(a.Y + r0 * k, yt, static_cast<uint32_t>(rows * k) * 4u);
-            bulk_commit();
+        if (NT & 1) {
+            constexpr int nt = NT - 1;
+            const float s0 = odd ? d[nt][0] : d[nt][2];
+            const float s1 = odd ? d[nt][1] : d[nt][3];
+            const float v0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+            const float v1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+            const int row = odd ? g + 8 : g;
+            const int c0 = 8 * nt + 2 * (odd ? t - 1 : t);
+            const float4 v = odd ? make_float4(v0, v1, d[nt][2], d[nt][3]) : make_float4(d[nt][0], d[nt][1], v0, v1);
+            if (row < rows && c0 + 4 <= k) red_add_v4(a.Y + (r0 + row) * k + c0, v.x, v.y, v.z, v.w);
         }
     };
 
@@ -330,7 +328,6 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
                 mbar_wait_bounded(&ws->bar[ss], (phases >> ss) & 1u);
                 ss = (ss + 1 == S) ? 0 : ss + 1;
             }
-            if (lane == 0) bulk_wait<0>();
             return;
         }
         phases ^= 1u << s;
@@ -470,8 +467,8 @@ __global__ void __launch_bounds__(SpmmCfg<NT>::WARPS * 32, SpmmCfg<NT>::MINB) k_
         s = (s + 1 == S) ? 0 : s + 1;
     }
     if (cur_rb >= 0) reduce_tile(yr, cur_rb * TILE, cur_rows);
-    if (lane == 0) bulk_wait<0>();   // reduces complete before the warp's shared memory goes away
 }
+
 
 // ---------------------------------------------------------------------------
 // Simple kernel for any k (1..32) and any alignment, float or double vectors:
