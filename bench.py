@@ -383,7 +383,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": recorded_traffic(args.workload),
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "kernel": "k_spmm_sym_tiled<2, 16> (k=16)", "alg_bytes_per_launch": B,
+                "kernel": f"k_spmm_sym_tiled<{(k + 7) // 8}, {k if k in (8, 16, 20, 32) else 0}> (k={k})",
+                "alg_bytes_per_launch": B,
                 "kernel_ms": round(spmm_ms, 4)}
 
     solves = None

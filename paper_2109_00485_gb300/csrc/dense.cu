@@ -319,7 +319,7 @@ __device__ __forceinline__ void gt_stage(const float *const *bp, const int *bcol
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// GT_TPW: most N-tiles per warp (1, 2 or 4)
+// GT_TPW: most N-tiles per warp (1, 2, 4 or 8)
 template <int GT_TPW>
 __global__ void __launch_bounds__(384) k_gram_tc(int64_t n, int k, int na, GemmBlocks<float> a, int nb,
                                                  GemmBlocks<float> b, double *M, int MT, int NT, int WN) {
@@ -1509,7 +1509,7 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
         const int MT = (ma + 15) / 16, NT = (mb + 7) / 8;
         const int WN = std::min(NT, (MT == 5) ? 2 : std::max(1, 12 / MT));   // warps per M-tile
         const int tpw = (NT + WN - 1) / WN;
-        if (k % 4 == 0 && aligned && ma <= 96 && mb <= 192 && tpw <= 4) {
+        if (k % 4 == 0 && aligned && ma <= 96 && mb <= 192 && tpw <= 8) {
             const int W = MT * WN;
             auto stride = [](int cols) { return cols + ((24 - cols % 32) + 32) % 32; };
             const size_t smem = sizeof(float) * 2 * GT_ROWS * (stride(16 * MT) + stride(8 * NT));
@@ -1520,6 +1520,8 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
                     e = cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
                 if (e == cudaSuccess)
                     e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(k_gram_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
                 if (e != cudaSuccess) return e;
                 attr = true;
             }
@@ -1530,7 +1532,8 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
             if (blocks < 1) blocks = 1;
             if (tpw == 1) k_gram_tc<1><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
             else if (tpw == 2) k_gram_tc<2><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
-            else k_gram_tc<4><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
+            else if (tpw <= 4) k_gram_tc<4><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
+            else k_gram_tc<8><<<blocks, W * 32, smem, s>>>(n, k, na, a, nb, b, M, MT, NT, WN);
             return cudaGetLastError();
         }
     }

@@ -49,10 +49,11 @@ constexpr int HS = 20;   // row stride of the scattered tile (fragment loads of 
 template <int NT>
 struct SpmmCfg {
     static constexpr int K = 8 * NT;
-    static constexpr int STAGES = SPMM_STAGES;
+    // k <= 16: four stages; k = 17..24: three, so that two blocks still fit
+    static constexpr int STAGES = NT <= 2 ? SPMM_STAGES : (NT == 3 ? 3 : SPMM_STAGES);
     static constexpr int WARPS = SPMM_WARPS;
-    // two blocks fit in shared memory only up to k = 16
-    static constexpr int MINB = NT <= 2 ? SPMM_MINB : 1;
+    // two blocks fit in shared memory up to k = 24 (three stages past 16)
+    static constexpr int MINB = NT <= 3 ? SPMM_MINB : 1;
 };
 
 // Shared memory of one warp.  A partial chunk is scattered into the stage
