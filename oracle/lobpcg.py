@@ -42,7 +42,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import cholesky, gershgorin, jacobi_eig, spmm_tri
-from .precond import apply_bjacobi, apply_diag, diag_of, tile_eigs
+from .precond import apply_bjacobi, apply_diag, apply_fom, diag_of, tile_eigs
 
 
 class RRFailure(RuntimeError):
@@ -149,10 +149,11 @@ class Result:
 
 def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
            precond: str = "diag", resid_mode: int = 0, tile: int = 64,
-           precond_fn=None, max_explicit_restarts: int = 5) -> Result:
+           precond_fn=None, max_explicit_restarts: int = 5, fom_steps: int = 4) -> Result:
     """FP64 block LOBPCG on the symmetric H stored as its lower triangle ``A``.
 
-    ``precond``: "none", "diag", "bjacobi" (64-row tiles) or "custom"
+    ``precond``: "none", "diag", "bjacobi" (64-row tiles), "fom" (``fom_steps``
+    FOM iterations per 64-row tile) or "custom"
     (``precond_fn(R, theta) -> W``).  Returns the nev leftmost Ritz pairs."""
     X0 = np.asarray(X0, dtype=np.float64)
     n, k = X0.shape
@@ -164,6 +165,8 @@ def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
     elif precond == "bjacobi":
         eigs = tile_eigs(A, tile)
         K = lambda R, th: apply_bjacobi(A, R, th, tile, eigs)
+    elif precond == "fom":
+        K = lambda R, th: apply_fom(A, R, th, fom_steps, tile)
     elif precond == "none":
         K = lambda R, th: R.copy()
     elif precond == "custom":

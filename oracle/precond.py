@@ -10,13 +10,24 @@ each shift close to one desired eigenvalue.  Readings taken here:
   * "diag" is the tile size 1 case: w_ij = r_ij / g(d_i - theta_j);
   * "bjacobi" solves each 64-row tile exactly, (H_T - theta_j I) w_T = r_T,
     through the eigendecomposition H_T = Q diag(lam) Q^T with the same guard
-    applied to lam - theta_j (the paper uses 3-5 FOM iterations instead).
+    applied to lam - theta_j;
+  * "fom" is the paper's own K^{-1}: a few iterations (three to five,
+    Section 3.3) of the Full Orthogonalization Method on each 64-row shifted
+    tile, every column of R its own Krylov space, x_0 = 0.  FOM is the
+    Arnoldi process (modified Gram-Schmidt) followed by the Galerkin solve
+    H_s y = beta e_1, x = V_s y.  Readings: the Arnoldi process stops early
+    (s = j) when h_{j+1,j} <= 1e-6 ||M v_j|| (the Krylov space is invariant);
+    the small Hessenberg system is solved by elimination without row
+    exchanges, each pivot guarded with g() like the tiles above, so that one
+    step reduces to the shifted Rayleigh quotient of r.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from . import dense_block, diagonal, jacobi_eig, lu_solve
+
+FOM_BREAKDOWN = 1e-6
 
 
 def guard(t: np.ndarray, theta: np.ndarray) -> np.ndarray:
@@ -73,6 +84,72 @@ def tile_solve_lu(A, t: int, r: np.ndarray, theta: float, tile: int = 64) -> np.
     m = min(tile, A.n - t * tile)
     B = dense_block(A, t * tile, m) - theta * np.eye(m)
     return lu_solve(B, r)
+
+
+def hessenberg_solve_guarded(Hs: np.ndarray, beta: float, theta: float) -> np.ndarray:
+    """y with H_s y = beta e_1 for an upper Hessenberg H_s (s x s): Gaussian
+    elimination without row exchanges (one multiplier per column, from the
+    subdiagonal), pivots guarded by g(), then back substitution."""
+    s = Hs.shape[0]
+    U = np.array(Hs, dtype=np.float64, copy=True)
+    b = np.zeros(s)
+    b[0] = beta
+    th = np.array([theta])
+    for i in range(s):
+        U[i, i] = guard(np.array([U[i, i]]), th)[0]
+        if i + 1 < s:
+            l = U[i + 1, i] / U[i, i]
+            U[i + 1, i:] -= l * U[i, i:]
+            b[i + 1] -= l * b[i]
+    y = np.zeros(s)
+    for i in range(s - 1, -1, -1):
+        y[i] = (b[i] - U[i, i + 1:] @ y[i + 1:]) / U[i, i]
+    return y
+
+
+def fom_solve(M: np.ndarray, r: np.ndarray, steps: int, theta: float, trace: dict | None = None) -> np.ndarray:
+    """Approximate M^{-1} r by ``steps`` iterations of FOM from x_0 = 0
+    (Arnoldi with modified Gram-Schmidt, then the Galerkin solve).  ``trace``
+    (optional) receives the basis V_s and the Hessenberg matrix H_s."""
+    m = M.shape[0]
+    beta = float(np.linalg.norm(r))
+    if beta == 0.0:
+        return np.zeros(m)
+    V = np.zeros((m, steps + 1))
+    H = np.zeros((steps + 1, steps))
+    V[:, 0] = r / beta
+    s = steps
+    for j in range(steps):
+        w = M @ V[:, j]
+        wnorm = float(np.linalg.norm(w))
+        for i in range(j + 1):                       # modified Gram-Schmidt
+            H[i, j] = w @ V[:, i]
+            w = w - H[i, j] * V[:, i]
+        H[j + 1, j] = float(np.linalg.norm(w))
+        if H[j + 1, j] <= FOM_BREAKDOWN * wnorm:      # invariant Krylov space: stop at s = j + 1
+            s = j + 1
+            break
+        if j + 1 < steps:
+            V[:, j + 1] = w / H[j + 1, j]
+    y = hessenberg_solve_guarded(H[:s, :s], beta, theta)
+    if trace is not None:
+        trace["V"] = V[:, :s].copy()
+        trace["H"] = H[:s + 1, :s].copy()
+    return V[:, :s] @ y
+
+
+def apply_fom(A, R: np.ndarray, theta: np.ndarray, steps: int = 4, tile: int = 64) -> np.ndarray:
+    """w_T,j = FOM_steps(H_T - theta_j I, r_T,j) for every 64-row diagonal tile
+    T and column j (a ragged last tile is its own smaller system)."""
+    n, k = R.shape
+    W = np.zeros((n, k))
+    for t in range((n + tile - 1) // tile):
+        m = min(tile, n - t * tile)
+        B = dense_block(A, t * tile, m)
+        for j in range(k):
+            W[t * tile:t * tile + m, j] = fom_solve(B - theta[j] * np.eye(m), R[t * tile:t * tile + m, j],
+                                                    steps, float(theta[j]))
+    return W
 
 
 def diag_of(A) -> np.ndarray:
