@@ -149,11 +149,12 @@ class Result:
 
 def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
            precond: str = "diag", resid_mode: int = 0, tile: int = 64,
-           precond_fn=None, max_explicit_restarts: int = 5, fom_steps: int = 4) -> Result:
+           precond_fn=None, max_explicit_restarts: int = 5, fom_steps: int = 4,
+           fom_tile_ptr=None) -> Result:
     """FP64 block LOBPCG on the symmetric H stored as its lower triangle ``A``.
 
     ``precond``: "none", "diag", "bjacobi" (64-row tiles), "fom" (``fom_steps``
-    FOM iterations per 64-row tile) or "custom"
+    FOM iterations per diagonal tile: ``fom_tile_ptr``, else 64-row tiles) or "custom"
     (``precond_fn(R, theta) -> W``).  Returns the nev leftmost Ritz pairs."""
     X0 = np.asarray(X0, dtype=np.float64)
     n, k = X0.shape
@@ -166,7 +167,7 @@ def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
         eigs = tile_eigs(A, tile)
         K = lambda R, th: apply_bjacobi(A, R, th, tile, eigs)
     elif precond == "fom":
-        K = lambda R, th: apply_fom(A, R, th, fom_steps, tile)
+        K = lambda R, th: apply_fom(A, R, th, fom_steps, tile, fom_tile_ptr)
     elif precond == "none":
         K = lambda R, th: R.copy()
     elif precond == "custom":

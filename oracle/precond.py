@@ -17,9 +17,11 @@ each shift close to one desired eigenvalue.  Readings taken here:
     Arnoldi process (modified Gram-Schmidt) followed by the Galerkin solve
     H_s y = beta e_1, x = V_s y.  Readings: the Arnoldi process stops early
     (s = j) when h_{j+1,j} <= 1e-6 ||M v_j|| (the Krylov space is invariant);
-    the small Hessenberg system is solved by elimination without row
-    exchanges, each pivot guarded with g() like the tiles above, so that one
-    step reduces to the shifted Rayleigh quotient of r.
+    the small Hessenberg system (the paper leaves its solution open) is
+    solved by Gaussian elimination with partial pivoting -- a row exchange
+    between neighbouring rows where the subdiagonal entry is the larger --
+    each pivot guarded with g() like the tiles above, so that one step
+    reduces to the shifted Rayleigh quotient of r.
 """
 from __future__ import annotations
 
@@ -88,14 +90,18 @@ def tile_solve_lu(A, t: int, r: np.ndarray, theta: float, tile: int = 64) -> np.
 
 def hessenberg_solve_guarded(Hs: np.ndarray, beta: float, theta: float) -> np.ndarray:
     """y with H_s y = beta e_1 for an upper Hessenberg H_s (s x s): Gaussian
-    elimination without row exchanges (one multiplier per column, from the
-    subdiagonal), pivots guarded by g(), then back substitution."""
+    elimination with partial pivoting (column i has nonzeros in rows i and
+    i + 1 only, so a pivot search is one comparison and an exchange of the two
+    rows), pivots guarded by g(), then back substitution."""
     s = Hs.shape[0]
     U = np.array(Hs, dtype=np.float64, copy=True)
     b = np.zeros(s)
     b[0] = beta
     th = np.array([theta])
     for i in range(s):
+        if i + 1 < s and abs(U[i + 1, i]) > abs(U[i, i]):
+            U[[i, i + 1], i:] = U[[i + 1, i], i:]
+            b[[i, i + 1]] = b[[i + 1, i]]
         U[i, i] = guard(np.array([U[i, i]]), th)[0]
         if i + 1 < s:
             l = U[i + 1, i] / U[i, i]
@@ -138,17 +144,28 @@ def fom_solve(M: np.ndarray, r: np.ndarray, steps: int, theta: float, trace: dic
     return V[:, :s] @ y
 
 
-def apply_fom(A, R: np.ndarray, theta: np.ndarray, steps: int = 4, tile: int = 64) -> np.ndarray:
-    """w_T,j = FOM_steps(H_T - theta_j I, r_T,j) for every 64-row diagonal tile
-    T and column j (a ragged last tile is its own smaller system)."""
+def tile_bounds(n: int, tile: int = 64, tile_ptr=None) -> np.ndarray:
+    """Row partition of the diagonal tiles: the given ``tile_ptr`` (strictly
+    increasing, 0 .. n), else consecutive ``tile``-row tiles."""
+    if tile_ptr is None:
+        return np.append(np.arange(0, n, tile, dtype=np.int64), np.int64(n))
+    tp = np.asarray(tile_ptr, dtype=np.int64)
+    assert tp[0] == 0 and tp[-1] == n and np.all(np.diff(tp) > 0)
+    return tp
+
+
+def apply_fom(A, R: np.ndarray, theta: np.ndarray, steps: int = 4, tile: int = 64, tile_ptr=None) -> np.ndarray:
+    """w_T,j = FOM_steps(H_T - theta_j I, r_T,j) for every diagonal tile T and
+    column j.  Tiles: ``tile_ptr`` (any sizes, as the paper's diagonal tiles of
+    1 to thousands of rows), else 64-row tiles with a ragged last one."""
     n, k = R.shape
     W = np.zeros((n, k))
-    for t in range((n + tile - 1) // tile):
-        m = min(tile, n - t * tile)
-        B = dense_block(A, t * tile, m)
+    tp = tile_bounds(n, tile, tile_ptr)
+    for t in range(tp.size - 1):
+        a, m = int(tp[t]), int(tp[t + 1] - tp[t])
+        B = dense_block(A, a, m)
         for j in range(k):
-            W[t * tile:t * tile + m, j] = fom_solve(B - theta[j] * np.eye(m), R[t * tile:t * tile + m, j],
-                                                    steps, float(theta[j]))
+            W[a:a + m, j] = fom_solve(B - theta[j] * np.eye(m), R[a:a + m, j], steps, float(theta[j]))
     return W
 
 

@@ -119,6 +119,28 @@ def u64(m: int, seed: int, tag: int) -> np.ndarray:
     return out
 
 
+def tile_partition(n: int, seed: int, median: float = 200.0, sigma: float = 1.0, max_size: int = 6000,
+                   tag: int = 7) -> np.ndarray:
+    """Row partition into diagonal tiles of varying size (int64 boundaries,
+    0 .. n): sizes round(median * exp(sigma * z)), z ~ N(0,1) seeded, clipped
+    to [1, max_size], the last tile cut at n.  Stands in for the paper's
+    diagonal tiles, which run from 1 to ~6000 rows, mostly a few hundred
+    (Section 4, diagonal tile size histogram)."""
+    sizes = []
+    total, drawn = 0, 0
+    while total < n:
+        z = normals(max(64, n // max(1, int(median)) + 64), seed, tag + drawn)
+        drawn += 1
+        for v in z:
+            sz = int(min(max(round(median * float(np.exp(sigma * v))), 1), max_size))
+            sz = min(sz, n - total)
+            sizes.append(sz)
+            total += sz
+            if total >= n:
+                break
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+
 def csr_from_dense_lower(a: np.ndarray, fp32: bool = False) -> CSR:
     """Lower-triangle CSR of a dense symmetric matrix (explicit zeros dropped,
     diagonal always kept).  Used to build small hand-made test matrices."""

@@ -94,6 +94,10 @@ def test_degenerate_inputs():
     r = np.arange(1.0, 17.0)
     assert np.allclose(fom_solve(np.zeros((16, 16)), r, 4, 0.0), r / 1e-3, rtol=1e-15, atol=0)
     assert np.allclose(fom_solve(np.zeros((16, 16)), r, 4, -5000.0), r / 5.0, rtol=1e-15, atol=0)
+    # a zero leading pivot of a nonsingular H_s: [[0, 1], [1, 0]] from M = the
+    # 2 x 2 exchange matrix and r = e_1 -- the row exchange solves it exactly
+    M2 = np.array([[0.0, 1.0], [1.0, 0.0]])
+    assert np.array_equal(fom_solve(M2, np.array([3.0, 0.0]), 2, 0.0), [0.0, 3.0])
 
 
 def test_apply_fom_per_tile_and_full_dimension_limit():
@@ -124,3 +128,34 @@ def test_lobpcg_with_fom_preconditioner_vs_library():
     r = olb.lobpcg(A, X0, 5, tol=1e-10, maxiter=2000, precond="fom")
     assert r.converged
     assert np.max(np.abs(r.evals - lam[:5]) / np.maximum(np.abs(lam[:5]), 1e-3)) < 1e-10
+
+
+def test_apply_fom_tile_partitions():
+    from oracle.precond import apply_diag, tile_bounds
+    A = synth.tile_matrix(150, 40, seed=12)
+    R = synth.normal_block(150, 3, seed=2)
+    th = np.array([-100.0, -50.0, -75.0])
+    # an explicit partition into the default 64-row tiles is the default
+    assert np.array_equal(apply_fom(A, R, th, 4, tile_ptr=[0, 64, 128, 150]), apply_fom(A, R, th, 4))
+    assert np.array_equal(tile_bounds(150), [0, 64, 128, 150])
+    # 1-row tiles: one FOM step on a 1 x 1 system is the diagonal preconditioner
+    th2 = np.array([0.5, 3.0, -1.0])
+    W1 = apply_fom(A, R, th2, 4, tile_ptr=np.arange(151))
+    assert np.allclose(W1, apply_diag(oracle.diagonal(A), R, th2), rtol=1e-14, atol=0)
+    # tiles of varying size (5, 12, 83, 50 rows) with as many steps as rows:
+    # each tile's exact shifted solve
+    tp = [0, 5, 17, 100, 150]
+    Wv = apply_fom(A, R, th, 100, tile_ptr=tp)
+    for a, b in zip(tp[:-1], tp[1:]):
+        B = oracle.dense_block(A, a, b - a)
+        for j in range(3):
+            y = np.linalg.solve(B - th[j] * np.eye(b - a), R[a:b, j])
+            assert np.linalg.norm(Wv[a:b, j] - y) <= 1e-9 * np.linalg.norm(y)
+
+
+def test_tile_partition_generator():
+    tp = synth.tile_partition(100_000, 3)
+    d = np.diff(tp)
+    assert tp[0] == 0 and tp[-1] == 100_000 and np.all(d >= 1) and np.all(d <= 6000)
+    assert 100 <= np.median(d) <= 400                    # mostly a few hundred rows
+    assert np.array_equal(tp, synth.tile_partition(100_000, 3))
