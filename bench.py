@@ -211,7 +211,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "mlp")):
+def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "mlp")):
     """Time-to-solution (relative residual 1e-6, nev pairs) from a host X0,
     through lobpcg_solve; create (matrix tiling, preconditioner set-up) is
     timed separately.  The learned form ("mlp") is first trained on pairs

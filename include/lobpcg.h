@@ -77,7 +77,8 @@ typedef struct {
     int32_t nev;         /* wanted eigenpairs, 1..k */
     int32_t maxiter;     /* iteration limit */
     double tol;          /* relative residual tolerance */
-    int32_t precond;     /* 0 none, 1 diagonal, 2 block-Jacobi (64-row tiles), 3 learned MLP */
+    int32_t precond;     /* 0 none, 1 diagonal, 2 block-Jacobi (64-row tiles), 3 learned MLP,
+                            4 FOM on the shifted 64-row tiles (Section 3.3) */
     int32_t resid_mode;  /* 0: ||r||/(max(|theta|,1e-12||H||_G)||x||), 1: ||r||/(||H||_G||x||) */
     int32_t polish_fp64; /* 1: finish with FP64 vectors once FP32 stagnates */
     int32_t tile_format; /* 0: every stored entry keeps its index word and value word (8 bytes,
@@ -87,6 +88,15 @@ typedef struct {
                             Section 3.3 keeps 2-byte local indices in its compressed sparse
                             blocks for the same reason: fewer index bytes per entry) */
     uint64_t seed;
+    int32_t fom_steps;   /* FOM iterations per tile for precond 4: 1..6, 0 = 4 (Section 3.3:
+                            three to five are enough) */
+    int32_t reserved;    /* must be 0 */
+    const int64_t *fom_tile_ptr; /* precond 4: row partition into diagonal tiles, HOST memory,
+                            fom_ntiles + 1 strictly increasing boundaries from 0 to n (tile t
+                            is rows [fom_tile_ptr[t], fom_tile_ptr[t+1])), read during create
+                            only; any sizes (the paper's tiles run from 1 to thousands of
+                            rows).  NULL: consecutive 64-row tiles. */
+    int64_t fom_ntiles;  /* tiles in fom_tile_ptr (ignored when it is NULL) */
 } lobpcg_params;
 
 /* Counters of one lobpcg_solve. */
@@ -190,6 +200,16 @@ LOBPCG_API lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double
  *           k <= params.k.  A tile column whose correction is not finite
  *           keeps its mode-1 value; a correction longer (over the tile) than
  *           the mode-1 value is scaled down to that length.
+ *   mode 4: params.fom_steps iterations of the Full Orthogonalization Method
+ *           (Section 3.3) on (H_T - theta_j I) w_T = r_T for every diagonal
+ *           tile T and column j, from w = 0: Arnoldi basis of
+ *           K_s(H_T - theta_j I, r_T), then the Galerkin solve of the small
+ *           Hessenberg system (Gaussian elimination with partial pivoting,
+ *           pivots guarded by g).  The Krylov space of a column stops growing when
+ *           the new basis direction has norm <= 1e-6 of (H_T - theta_j I) v
+ *           (an invariant subspace).  Tiles: params.fom_tile_ptr (else 64
+ *           rows).  Needs params.precond == 4 at create; k <= params.k when
+ *           a tile is longer than 64 rows (its scratch is sized at create).
  *   R, W  : float32 n x k row-major, device (may be the same buffer)
  *   theta : float64[k], device
  */

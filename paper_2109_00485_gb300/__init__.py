@@ -24,7 +24,7 @@ STATUS = {
 }
 MEM_DEVICE, MEM_HOST = 0, 1
 MLP_NPARAM = 49728      # W1 [256][129] | b1 [256] | W2 [64][256] | b2 [64]
-PRECOND = {"none": 0, "diag": 1, "bjacobi": 2, "mlp": 3}
+PRECOND = {"none": 0, "diag": 1, "bjacobi": 2, "mlp": 3, "fom": 4}
 
 
 class LobpcgError(RuntimeError):
@@ -42,7 +42,9 @@ class _Matrix(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("nev", ctypes.c_int32), ("maxiter", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("precond", ctypes.c_int32), ("resid_mode", ctypes.c_int32),
-                ("polish_fp64", ctypes.c_int32), ("tile_format", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("polish_fp64", ctypes.c_int32), ("tile_format", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("fom_steps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("fom_tile_ptr", ctypes.c_void_p),
+                ("fom_ntiles", ctypes.c_int64)]
 
 
 class _Stats(ctypes.Structure):
@@ -372,7 +374,8 @@ def lobpcg_last_error() -> str:
 
 
 def make_params(k: int, nev: int | None = None, maxiter: int = 1000, tol: float = 1e-6, precond="diag",
-                resid_mode: int = 0, polish_fp64: int = 1, seed: int = 0, tile_format: int = 0) -> _Params:
+                resid_mode: int = 0, polish_fp64: int = 1, seed: int = 0, tile_format: int = 0,
+                fom_steps: int = 0, fom_tile_ptr=None) -> _Params:
     p = _Params()
     p.k = k
     p.nev = k if nev is None else nev
@@ -383,6 +386,12 @@ def make_params(k: int, nev: int | None = None, maxiter: int = 1000, tol: float 
     p.polish_fp64 = polish_fp64
     p.tile_format = tile_format
     p.seed = seed & (2 ** 64 - 1)
+    p.fom_steps = fom_steps
+    if fom_tile_ptr is not None:
+        tp = np.ascontiguousarray(fom_tile_ptr, dtype=np.int64)
+        p._keep = tp                       # the array must outlive the create call
+        p.fom_tile_ptr = tp.ctypes.data
+        p.fom_ntiles = tp.size - 1
     return p
 
 

@@ -82,6 +82,17 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     if (P.k < 1 || P.k > 32) return fail(nullptr, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     if (P.nev < 1 || P.nev > P.k) return fail(nullptr, LOBPCG_ERR_ARG, "nev must be in [1, k]");
     if (P.tile_format != 0 && P.tile_format != 1) return fail(nullptr, LOBPCG_ERR_ARG, "tile_format must be 0 or 1");
+    if (P.precond < 0 || P.precond > 4) return fail(nullptr, LOBPCG_ERR_ARG, "precond must be 0..4");
+    if (P.fom_steps < 0 || P.fom_steps > 6) return fail(nullptr, LOBPCG_ERR_ARG, "fom_steps must be 0..6");
+    if (P.reserved != 0) return fail(nullptr, LOBPCG_ERR_ARG, "reserved must be 0");
+    if (P.precond == 4 && P.fom_tile_ptr) {
+        const int64_t *tp = P.fom_tile_ptr;
+        if (P.fom_ntiles < 1 || P.fom_ntiles > A->n) return fail(nullptr, LOBPCG_ERR_ARG, "fom_ntiles must be in [1, n]");
+        if (tp[0] != 0 || tp[P.fom_ntiles] != A->n)
+            return fail(nullptr, LOBPCG_ERR_ARG, "fom_tile_ptr must start at 0 and end at n");
+        for (int64_t t = 0; t < P.fom_ntiles; ++t)
+            if (tp[t + 1] <= tp[t]) return fail(nullptr, LOBPCG_ERR_ARG, "fom_tile_ptr must be strictly increasing");
+    }
 
     lobpcg_ctx *h = new (std::nothrow) lobpcg_ctx();
     if (!h) return fail(nullptr, LOBPCG_ERR_OOM, "host allocation failed");
@@ -138,6 +149,7 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
     if (e == cudaSuccess && st == LOBPCG_OK && (P.precond == 2 || P.precond == 3))
         e = bjacobi_setup(h, rp, cl, vl, A->val_is_fp64 != 0);   // the learned form trains on exact tile solves
     if (e == cudaSuccess && st == LOBPCG_OK && P.precond == 3) e = mlp_setup(h);
+    if (e == cudaSuccess && st == LOBPCG_OK && P.precond == 4) e = fom_setup(h, rp, cl, vl, A->val_is_fp64 != 0, P.fom_tile_ptr, P.fom_ntiles);
     if (e == cudaSuccess && st == LOBPCG_OK) e = solver_setup(h);
     if (e == cudaSuccess && st == LOBPCG_OK) e = cudaStreamSynchronize(h->stream);
     if (tmp) {
@@ -242,7 +254,10 @@ lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *the
     if (!h) return LOBPCG_ERR_ARG;
     if (!R || !W || !theta) return fail(h, LOBPCG_ERR_ARG, "R, W or theta is NULL");
     if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
-    if (mode < 0 || mode > 3) return fail(h, LOBPCG_ERR_ARG, "mode must be 0..3");
+    if (mode < 0 || mode > 4) return fail(h, LOBPCG_ERR_ARG, "mode must be 0..4");
+    if (mode == 4 && !h->fom.ready) return fail(h, LOBPCG_ERR_UNSUPPORTED, "FOM needs params.precond = 4 at create");
+    if (mode == 4 && h->fom.n_large && k > h->fom.scr_k)
+        return fail(h, LOBPCG_ERR_ARG, "FOM with tiles over 64 rows: k must be <= params.k");
     if (mode == 2 && !h->bj_Q) return fail(h, LOBPCG_ERR_UNSUPPORTED, "block-Jacobi needs params.precond = 2 at create");
     if (mode == 3 && !h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (mode == 3 && !h->mlp.ready) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner has no weights");

@@ -53,6 +53,36 @@ struct Tiled {
     float *diag = nullptr;   // d_i = h_ii (float32)
 };
 
+// Diagonal tiles of the FOM preconditioner (fom.cu).  Small tiles (<= 64
+// rows): dense FP32 64 x 64 blocks, both triangles, zero outside the m x m
+// corner, one per small tile in s_t0 order.  Large tiles (> 64 rows), in
+// decreasing size: the lower triangle of each tile as a CSR over the rows
+// of the large tiles packed one after another (tile q starts at packed row
+// l_base[q]), local column indices, cut into segments of <= 64 rows inside
+// one tile; scr holds the Krylov basis and work vector of every large-tile
+// row (7 blocks of large_rows x scr_k floats), acc the per-tile sums.
+struct FomTiles {
+    int64_t n_small = 0, n_large = 0, large_rows = 0, large_nnz = 0;
+    int32_t max_large = 0;
+    int64_t *s_t0 = nullptr;
+    int32_t *s_m = nullptr;
+    float *A = nullptr;
+    int64_t *l_t0 = nullptr;
+    int32_t *l_m = nullptr;
+    int64_t *l_base = nullptr;
+    int64_t *rp = nullptr;        // [large_rows + 1]
+    int32_t *col = nullptr;
+    float *val = nullptr;
+    float *scr = nullptr;
+    int32_t scr_k = 0;
+    int64_t n_seg = 0;
+    int64_t *seg_p0 = nullptr;
+    int32_t *seg_n = nullptr;
+    int32_t *seg_t = nullptr;
+    float *acc = nullptr;
+    bool ready = false;
+};
+
 }  // namespace lobpcg
 
 struct lobpcg_ctx {
@@ -71,6 +101,7 @@ struct lobpcg_ctx {
     size_t stage_k = 0;
     float *bj_Q = nullptr;       // block-Jacobi: per 64-row tile eigenvectors (64 x 64) and eigenvalues
     float *bj_lam = nullptr;
+    lobpcg::FomTiles fom;        // FOM preconditioner tiles (fom.cu)
     lobpcg::SolverState *solver = nullptr;  // workspaces of lobpcg_solve (solver.cu)
     lobpcg::Mlp mlp;                         // learned tile preconditioner (mlp.cu)
     std::string last_error;

@@ -6,6 +6,10 @@
 //   block-Jacobi: 64-row tiles solved exactly through their eigen-
 //                 decomposition H_T = Q diag(lam) Q^T (computed once, FP64
 //                 Jacobi, stored FP32): w_T = Q diag(1/g(lam - theta_j)) Q^T r_T
+//   FOM         : the paper's form: s steps (3-5 in Section 3.3) of the Full
+//                 Orthogonalization Method on each shifted 64-row tile
+//                 H_T - theta_j I, every column of R its own Krylov space
+//                 (x_0 = 0), all columns of a tile advanced together
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -215,6 +219,7 @@ cudaError_t precond_apply(const lobpcg_ctx *h, int mode, int k, const T *R, cons
             return mlp_apply(const_cast<lobpcg_ctx *>(h), k, R, theta, W, s);
         }
     }
+    if (mode == 4) return fom_apply<T>(h, k, R, theta, W, s);
     return cudaErrorInvalidValue;
 }
 

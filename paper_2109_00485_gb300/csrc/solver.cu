@@ -252,7 +252,7 @@ cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool has
                 CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
             }
         }
-        if (pmode == 3) CK(precond_apply<T>(h, 3, k, b.W, s->theta, b.W, h->stream));
+        if (pmode == 3 || pmode == 4) CK(precond_apply<T>(h, pmode, k, b.W, s->theta, b.W, h->stream));
         // orthonormalise W against X and itself
         CK(orth_pass<T>(h, s, b));
         CK(orth_pass<T>(h, s, b));
@@ -486,7 +486,7 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         if (res.iters >= max_iters) break;
         ++res.iters;
         // preconditioner (the diagonal one was applied in the residual)
-        if (pmode == 2 || pmode == 3) CK(precond_apply<float>(h, pmode, k, f.W, s->theta, f.W, h->stream));
+        if (pmode >= 2) CK(precond_apply<float>(h, pmode, k, f.W, s->theta, f.W, h->stream));
         CK(orth_pass<float>(h, s, f));
         CK(orth_pass<float>(h, s, f));
         CK(timed_spmm<float>(h, s, f.W, f.HW, k));
