@@ -57,8 +57,9 @@ def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
 def kernel_source_hash() -> str:
@@ -211,21 +212,69 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "mlp")):
+def fom_report(pkg, A, p, stream, sm_mhz: float) -> dict:
+    """The FOM preconditioner (Section 3.3) on its own: one application to a
+    seeded n x k block, 4 FOM steps, on 64-row tiles (k_fom_small) and on a
+    seeded partition into 5..6000-row tiles (mostly k_fl_* segment kernels);
+    CUDA events over 10 applications after 3 warm-ups.  The 64-row kernel is
+    bound by FP32 arithmetic: its algorithmic FLOPs are the products
+    2 * 64 * 64 * k per tile and step; the peak is 152 SMs x 128 FP32 lanes x
+    2 FLOP x the SM clock."""
+    import torch
+    k = p["k"]
+    R = torch.from_numpy(synth.normal_block(A.n, k, seed=41, fp32=True)).cuda()
+    th = torch.linspace(-2.0, 30.0, k, dtype=torch.float64, device="cuda")
+    tpv = synth.tile_partition(A.n, p["seed"])
+    out = {}
+    for label, tp in (("tiles64", None), ("variable", tpv)):
+        h = pkg.from_csr(A, k=k, nev=p["nev"], precond="fom", fom_steps=4, fom_tile_ptr=tp, stream=stream)
+        W = torch.empty_like(R)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                h.precond_apply(R, th, W, mode="fom")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                h.precond_apply(R, th, W, mode="fom")
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        h.destroy()
+        d = {"ms": round(ms, 4), "steps": 4, "k": k}
+        if tp is None:
+            nt = (A.n + 63) // 64
+            flops = nt * 4 * 2 * 64 * 64 * k
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            d.update({"kernel": "k_fom_small", "tiles": nt, "tflops": round(flops / (ms / 1e3) / 1e12, 2),
+                      "peak_tflops_fp32_alu": round(peak, 1), "peak_clock_mhz": sm_mhz,
+                      "frac": round(flops / (ms / 1e3) / 1e12 / peak, 4)})
+        else:
+            sizes = np.diff(tpv)
+            d.update({"tiles": int(sizes.size), "tiles_over_64_rows": int((sizes > 64).sum()),
+                      "rows_in_tiles_over_64": int(sizes[sizes > 64].sum()), "largest_tile": int(sizes.max()),
+                      "median_tile": float(np.median(sizes))})
+        out[label] = d
+    return out
+
+
+def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var", "mlp")):
     """Time-to-solution (relative residual 1e-6, nev pairs) from a host X0,
     through lobpcg_solve; create (matrix tiling, preconditioner set-up) is
     timed separately.  The learned form ("mlp") is first trained on pairs
     harvested from 20 block-Jacobi iterations from the same X0 (about 1M
     pairs, 5 epochs, Adam lr 1e-3): its training time is reported on its own
-    and added in."""
+    and added in.  "fom" runs 4 FOM steps per 64-row tile, "fom_var" the same
+    on a seeded partition into 5..6000-row tiles (synth.tile_partition)."""
     import torch
     out = {}
     X0 = synth.initial_guess(A, p["k"], seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
     for pc in precs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc, polish_fp64=1,
-                         stream=stream, seed=p["seed"])
+        extra = {"fom_tile_ptr": synth.tile_partition(A.n, p["seed"])} if pc == "fom_var" else {}
+        h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc.replace("_var", ""),
+                         polish_fp64=1, stream=stream, seed=p["seed"], **extra)
         torch.cuda.synchronize()
         t_create = time.perf_counter() - t0
         train = None
@@ -390,6 +439,9 @@ def main():
     solves = None
     if rank == 0 and not args.no_solves:
         solves = lobpcg_solves(pkg, A, p, stream)
+    fom = None
+    if rank == 0 and not args.no_solves:
+        fom = fom_report(pkg, A, p, stream, peaks["sm_max_mhz"])
     vonly = None
     if rank == 0 and not args.no_value_only and not args.no_solves:
         vonly = value_only_report(pkg, A, p, stream, spmm_ms, peaks["hbm_gbs"])
@@ -412,6 +464,7 @@ def main():
                 "gpu_launches": LAUNCHES_PER_ITERATION * args.steps,
                 "gflops_spmm": round(4.0 * k * nnz / (spmm_ms / 1e3) / 1e9, 1),
                 "lobpcg": solves,
+                "fom_apply": fom,
                 "value_only_tiles": vonly,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],
                            "padded_nnz": info["padded_nnz"], "warps": info["warps"]}}

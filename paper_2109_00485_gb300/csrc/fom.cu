@@ -18,7 +18,7 @@
 // dense in shared memory, every column's basis in registers); larger tiles
 // (the paper's run to thousands of rows) in the k_fl_* kernels: all large
 // tiles advance together, one grid-wide kernel per phase of a step over
-// 64-row segments, the tiles' lower triangles as a local CSR and the basis
+// 64-row segments, each tile as a local CSR of both triangles and the basis
 // vectors in a global scratch.
 #include <algorithm>
 #include <cstdint>
@@ -282,25 +282,29 @@ __global__ void __launch_bounds__(256) k_fom_small(int k, int steps, const int64
 // the whole GPU instead of one CTA (the paper notes that the spread of tile
 // sizes, 1 to thousands, unbalances its one-tile-per-gang loop).  Their
 // rows are packed one tile after another (packed row p) and cut into
-// segments of at most 64 rows inside one tile; each CTA (256 threads) takes
-// one segment, thread t serving column j = t % L and rows slot + RP q
-// (slot = t / L, RP = 256 / L).  Per-tile sums (norms and Gram-Schmidt
-// coefficients) are CTA partial sums added atomically into acc, one slot
-// set per step and pass, so that every later kernel reads complete sums and
-// replays the same per-column decisions from them.
-//   scratch: basis v_q at V + q nl k, work vector w at V + MS nl k,
-//            element (p, j) at p k + j
+// segments of at most 64 rows inside one tile; one CTA of 64 G threads takes
+// a segment, thread t serving row t / G of it and the four columns
+// 4 (t % G) .. 4 (t % G) + 3 (G = the power of two >= ceil(k / 4)), so
+// every vector access is one 16-byte load or store.  Per step: the product
+// (k_fl_matvec), two Gram-Schmidt passes (k_fl_dots1, k_fl_dots2) and the
+// next basis vector (k_fl_next).  Per-tile sums (norms
+// and Gram-Schmidt coefficients) are CTA partial sums added atomically into
+// acc, one slot set per step and pass; every later kernel reads complete
+// sums and replays the same per-column decisions from them.
+//   scratch: kp = k rounded up to 4 columns (the padding stays zero);
+//            basis v_q at V + q nl kp, work vector w at V + MS nl kp,
+//            element (p, j) at p kp + j
 //   acc    : [MS steps][2 passes][large tiles][NV][32]; slot i < MS is
 //            v_i . w, slot MS a squared norm; accb [large tiles][32] = ||r||^2
 struct LargeArgs {
-    int k, steps;
+    int k, kp, steps;
     int64_t nl, nlt;
     const int64_t *seg_p0;      // first packed row of each segment
     const int32_t *seg_n;       // rows of each segment (<= 64)
     const int32_t *seg_t;       // large tile of each segment
     const int64_t *l_t0;        // first matrix row of each large tile
     const int64_t *l_base;      // first packed row of each large tile
-    const int64_t *rp;          // local CSR of the tiles' lower triangles (packed rows)
+    const int64_t *rp;          // local CSR of each tile, both triangles (packed rows)
     const int32_t *lcol;        // column within the tile
     const float *lval;
     float *V;
@@ -313,6 +317,16 @@ constexpr int SEG = 64;
 __device__ __forceinline__ float *acc_at(const LargeArgs &a, int st, int pass, int tile) {
     return a.acc + ((static_cast<int64_t>(st) * 2 + pass) * a.nlt + tile) * (NV * 32);
 }
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 fma4v(float4 a, float4 x, float4 y) {
+    return make_float4(fmaf(a.x, x.x, y.x), fmaf(a.y, x.y, y.y), fmaf(a.z, x.z, y.z), fmaf(a.w, x.w, y.w));
+}
+__device__ __forceinline__ float comp(float4 v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
 
 // Replay steps 0 .. upto-1 of one tile column from the sums: H, s, and
 // whether the Krylov space still grows.  Every kernel that needs them calls
@@ -340,237 +354,279 @@ __device__ __forceinline__ void replay(const LargeArgs &a, int tile, int j, int 
     }
 }
 
-// CTA sum of NV partials per column, then one atomic add per column and used
-// slot (slots 0..nd-1 and MS) into dst[slot * 32 + j].
-template <int L>
-__device__ __forceinline__ void seg_sum_add(float (&v)[NV], int nd, float *red, float *dst, int k) {
-    const int tid = threadIdx.x;
-    colsum<L, 8>(v, red, tid >> 5, tid & 31);
-    if (tid < L && tid < k) {
+// Sum NV float4 partials over the 64 rows of a segment (lane groups of G in
+// a warp, then the 2G warps through shared memory) and add slots 0..nd-1
+// and MS of every real column atomically into dst[slot * 32 + j].
+template <int G>
+__device__ __forceinline__ void seg_sum_add(float4 (&v)[NV], int nd, float *red, float *dst, int k) {
+    constexpr int NWP = 2 * G;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = tid % G;
 #pragma unroll
-        for (int i = 0; i < MS; ++i)
-            if (i < nd) atomicAdd(dst + i * 32 + tid, v[i]);
-        atomicAdd(dst + MS * 32 + tid, v[MS]);
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            v[i].x += __shfl_xor_sync(0xffffffffu, v[i].x, o);
+            v[i].y += __shfl_xor_sync(0xffffffffu, v[i].y, o);
+            v[i].z += __shfl_xor_sync(0xffffffffu, v[i].z, o);
+            v[i].w += __shfl_xor_sync(0xffffffffu, v[i].w, o);
+        }
     }
+    if (lane < G) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) st4(red + (warp * NV + i) * 32 + 4 * g, v[i]);
+    }
+    __syncthreads();
+    if (tid < G) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (i < nd || i == MS) {
+                float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int w = 0; w < NWP; ++w) {
+                    const float4 x = ld4(red + (w * NV + i) * 32 + 4 * g);
+                    s.x += x.x;
+                    s.y += x.y;
+                    s.z += x.z;
+                    s.w += x.w;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (4 * g + c < k) atomicAdd(dst + i * 32 + 4 * g + c, comp(s, c));
+            }
+        }
+    }
+}
+
+struct SegPos {
+    int tile, n, r, g;
+    int64_t p0, p;
+};
+template <int G>
+__device__ __forceinline__ SegPos seg_pos(const LargeArgs &a) {
+    SegPos q;
+    q.tile = a.seg_t[blockIdx.x];
+    q.p0 = a.seg_p0[blockIdx.x];
+    q.n = a.seg_n[blockIdx.x];
+    q.r = threadIdx.x / G;
+    q.g = threadIdx.x % G;
+    q.p = q.p0 + q.r;
+    return q;
 }
 
 // ||r||^2 per tile column
-template <int L, typename T>
-__global__ void __launch_bounds__(256) k_fl_norm(LargeArgs a, const T *R) {
-    __shared__ float red[8 * NV * 32];
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t row0 = a.l_t0[tile] + (p0 - a.l_base[tile]);
-    float v[NV];
+template <int G, typename T>
+__global__ void __launch_bounds__(64 * G) k_fl_norm(LargeArgs a, const T *R) {
+    __shared__ __align__(16) float red[2 * G * NV * 32];
+    const SegPos q = seg_pos<G>(a);
+    float4 v[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = 0.f;
-    if (j < a.k)
-        for (int r = slot; r < n; r += RP) {
-            const float x = static_cast<float>(R[(row0 + r) * a.k + j]);
-            v[MS] = fmaf(x, x, v[MS]);
-        }
-    const int tid = threadIdx.x;
-    colsum<L, 8>(v, red, tid >> 5, tid & 31);
-    if (tid < L && tid < a.k) atomicAdd(a.accb + static_cast<int64_t>(tile) * 32 + tid, v[MS]);
+    for (int i = 0; i < NV; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.r < q.n) {
+        const int64_t row = a.l_t0[q.tile] + (q.p - a.l_base[q.tile]);
+        float x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = (4 * q.g + c < a.k) ? static_cast<float>(R[row * a.k + 4 * q.g + c]) : 0.f;
+        v[MS] = make_float4(x[0] * x[0], x[1] * x[1], x[2] * x[2], x[3] * x[3]);
+    }
+    // only slot MS is added: aim it at accb[tile][.] (the pointer stays inside acc)
+    seg_sum_add<G>(v, 0, red, a.accb + static_cast<int64_t>(q.tile) * 32 - MS * 32, a.k);
 }
 
 // v_0 = r / ||r||
-template <int L, typename T>
-__global__ void __launch_bounds__(256) k_fl_start(LargeArgs a, const T *R) {
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    if (j >= a.k) return;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t row0 = a.l_t0[tile] + (p0 - a.l_base[tile]);
-    const float beta = sqrtf(a.accb[static_cast<int64_t>(tile) * 32 + j]);
-    const float rb = beta > 0.f ? 1.f / beta : 0.f;
-    for (int r = slot; r < n; r += RP)
-        a.V[(p0 + r) * a.k + j] = static_cast<float>(R[(row0 + r) * a.k + j]) * rb;
+template <int G, typename T>
+__global__ void __launch_bounds__(64 * G) k_fl_start(LargeArgs a, const T *R) {
+    const SegPos q = seg_pos<G>(a);
+    if (q.r >= q.n || 4 * q.g >= a.kp) return;
+    const int64_t row = a.l_t0[q.tile] + (q.p - a.l_base[q.tile]);
+    float x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int j = 4 * q.g + c;
+        const float beta = (j < a.k) ? sqrtf(a.accb[static_cast<int64_t>(q.tile) * 32 + j]) : 0.f;
+        x[c] = (j < a.k && beta > 0.f) ? static_cast<float>(R[row * a.k + j]) / beta : 0.f;
+    }
+    st4(a.V + q.p * a.kp + 4 * q.g, make_float4(x[0], x[1], x[2], x[3]));
 }
 
-// w_p = sum_{c <= r} a_rc v_c - theta v_p (each row its own entries)
-template <int L>
-__global__ void __launch_bounds__(256) k_fl_gather(LargeArgs a, int st, const double *theta) {
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    if (j >= a.k) return;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x], base = a.l_base[tile];
-    const int n = a.seg_n[blockIdx.x];
-    const float th = static_cast<float>(theta[j]);
-    const float *v = a.V + static_cast<int64_t>(st) * a.nl * a.k;
-    float *w = a.V + static_cast<int64_t>(MS) * a.nl * a.k;
-    for (int r = slot; r < n; r += RP) {
-        const int64_t p = p0 + r;
-        const int64_t e0 = a.rp[p], e1 = a.rp[p + 1];
-        float s0 = 0.f, s1 = 0.f;
-        int64_t e = e0;
-        for (; e + 1 < e1; e += 2) {
-            s0 = fmaf(a.lval[e], v[(base + a.lcol[e]) * a.k + j], s0);
-            s1 = fmaf(a.lval[e + 1], v[(base + a.lcol[e + 1]) * a.k + j], s1);
-        }
-        if (e < e1) s0 = fmaf(a.lval[e], v[(base + a.lcol[e]) * a.k + j], s0);
-        w[p * a.k + j] = fmaf(-th, v[p * a.k + j], s0 + s1);
+// w = (H_T - theta I) v_st as a pure row gather over each tile's full
+// symmetric local CSR (both triangles, built at create): the segment's
+// rows of v_st are staged in shared memory, columns inside the segment are
+// read from there, the others from global memory; no atomics.
+template <int G>
+__global__ void __launch_bounds__(64 * G) k_fl_matvec(LargeArgs a, int st, const double *theta) {
+    __shared__ __align__(16) float sv[SEG * 4 * G];
+    const SegPos q = seg_pos<G>(a);
+    const int64_t base = a.l_base[q.tile], vs = a.nl * a.kp;
+    const float *v = a.V + st * vs;
+    const bool mine = q.r < q.n && 4 * q.g < a.kp;
+    const int seg0 = static_cast<int>(q.p0 - base);          // first tile row of the segment
+    float4 vp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) vp = ld4(v + q.p * a.kp + 4 * q.g);
+    st4(sv + q.r * 4 * G + 4 * q.g, vp);
+    __syncthreads();
+    if (!mine) return;
+    float th[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) th[c] = (4 * q.g + c < a.k) ? static_cast<float>(theta[4 * q.g + c]) : 0.f;
+    float4 s0 = make_float4(-th[0] * vp.x, -th[1] * vp.y, -th[2] * vp.z, -th[3] * vp.w);
+    float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t e1 = a.rp[q.p + 1];
+    int64_t e = a.rp[q.p];
+    for (; e + 1 < e1; e += 2) {
+        const int c0 = a.lcol[e] - seg0, c1 = a.lcol[e + 1] - seg0;
+        const float a0 = a.lval[e], a1 = a.lval[e + 1];
+        const float4 x0 = (c0 >= 0 && c0 < q.n) ? ld4(sv + c0 * 4 * G + 4 * q.g)
+                                               : ld4(v + (q.p0 + c0) * a.kp + 4 * q.g);
+        const float4 x1 = (c1 >= 0 && c1 < q.n) ? ld4(sv + c1 * 4 * G + 4 * q.g)
+                                               : ld4(v + (q.p0 + c1) * a.kp + 4 * q.g);
+        s0 = fma4(a0, x0, s0);
+        s1 = fma4(a1, x1, s1);
     }
-}
-
-// w_c += a_rc v_r for the entries below the diagonal (atomic: rows of other
-// segments of the tile)
-template <int L>
-__global__ void __launch_bounds__(256) k_fl_scatter(LargeArgs a, int st) {
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    if (j >= a.k) return;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x], base = a.l_base[tile];
-    const int n = a.seg_n[blockIdx.x];
-    const float *v = a.V + static_cast<int64_t>(st) * a.nl * a.k;
-    float *w = a.V + static_cast<int64_t>(MS) * a.nl * a.k;
-    for (int r = slot; r < n; r += RP) {
-        const int64_t p = p0 + r;
-        const int lr = static_cast<int>(p - base);
-        const float vr = v[p * a.k + j];
-        for (int64_t e = a.rp[p]; e < a.rp[p + 1]; ++e) {
-            const int c = a.lcol[e];
-            if (c < lr) atomicAdd(&w[(base + c) * a.k + j], a.lval[e] * vr);
-        }
+    if (e < e1) {
+        const int c0 = a.lcol[e] - seg0;
+        const float4 x0 = (c0 >= 0 && c0 < q.n) ? ld4(sv + c0 * 4 * G + 4 * q.g)
+                                               : ld4(v + (q.p0 + c0) * a.kp + 4 * q.g);
+        s0 = fma4(a.lval[e], x0, s0);
     }
+    st4(a.V + MS * vs + q.p * a.kp + 4 * q.g, make_float4(s0.x + s1.x, s0.y + s1.y, s0.z + s1.z, s0.w + s1.w));
 }
 
 // pass 1 partial sums: v_i . w (i <= st) and ||w||^2
-template <int L>
-__global__ void __launch_bounds__(256) k_fl_dots1(LargeArgs a, int st) {
-    __shared__ float red[8 * NV * 32];
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t vs = a.nl * a.k;
-    const float *w = a.V + MS * vs;
-    float v[NV];
+template <int G>
+__global__ void __launch_bounds__(64 * G) k_fl_dots1(LargeArgs a, int st) {
+    __shared__ __align__(16) float red[2 * G * NV * 32];
+    const SegPos q = seg_pos<G>(a);
+    const int64_t vs = a.nl * a.kp;
+    float4 v[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = 0.f;
-    if (j < a.k)
-        for (int r = slot; r < n; r += RP) {
-            const int64_t o = (p0 + r) * a.k + j;
-            const float x = w[o];
+    for (int i = 0; i < NV; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.r < q.n && 4 * q.g < a.kp) {
+        const int64_t o = q.p * a.kp + 4 * q.g;
+        const float4 x = ld4(a.V + MS * vs + o);
 #pragma unroll
-            for (int i = 0; i < MS; ++i)
-                if (i <= st) v[i] = fmaf(a.V[i * vs + o], x, v[i]);
-            v[MS] = fmaf(x, x, v[MS]);
-        }
-    seg_sum_add<L>(v, st + 1, red, acc_at(a, st, 0, tile), a.k);
+        for (int i = 0; i < MS; ++i)
+            if (i <= st) v[i] = fma4v(ld4(a.V + i * vs + o), x, v[i]);
+        v[MS] = fma4v(x, x, v[MS]);
+    }
+    seg_sum_add<G>(v, st + 1, red, acc_at(a, st, 0, q.tile), a.k);
 }
 
 // w1 = w - V h (stored) and the pass 2 partial sums v_i . w1, ||w1||^2
-template <int L>
-__global__ void __launch_bounds__(256) k_fl_dots2(LargeArgs a, int st) {
-    __shared__ float red[8 * NV * 32];
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t vs = a.nl * a.k;
-    float *w = a.V + MS * vs;
-    float h[MS];
-    const float *a1 = acc_at(a, st, 0, tile);
+template <int G>
+__global__ void __launch_bounds__(64 * G) k_fl_dots2(LargeArgs a, int st) {
+    __shared__ __align__(16) float red[2 * G * NV * 32];
+    const SegPos q = seg_pos<G>(a);
+    const int64_t vs = a.nl * a.kp;
+    float4 v[NV];
 #pragma unroll
-    for (int i = 0; i < MS; ++i) h[i] = (i <= st && j < a.k) ? a1[i * 32 + j] : 0.f;
-    float v[NV];
+    for (int i = 0; i < NV; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.r < q.n && 4 * q.g < a.kp) {
+        const float *a1 = acc_at(a, st, 0, q.tile) + 4 * q.g;
+        const int64_t o = q.p * a.kp + 4 * q.g;
+        float4 vq[MS];
+        float4 x = ld4(a.V + MS * vs + o);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = 0.f;
-    if (j < a.k)
-        for (int r = slot; r < n; r += RP) {
-            const int64_t o = (p0 + r) * a.k + j;
-            float vq[MS];
-            float x = w[o];
+        for (int i = 0; i < MS; ++i) {
+            if (i <= st) {
+                vq[i] = ld4(a.V + i * vs + o);
+                const float4 h = ld4(a1 + i * 32);
+                x = fma4v(make_float4(-h.x, -h.y, -h.z, -h.w), vq[i], x);
+            }
+        }
+        st4(a.V + MS * vs + o, x);
+#pragma unroll
+        for (int i = 0; i < MS; ++i)
+            if (i <= st) v[i] = fma4v(vq[i], x, v[i]);
+        v[MS] = fma4v(x, x, v[MS]);
+    }
+    seg_sum_add<G>(v, st + 1, red, acc_at(a, st, 1, q.tile), a.k);
+}
+
+// v_{st+1} = (w1 - V c) / h_{st+1,st}, zero once the column has stopped.
+// One thread per column replays the tile's history; the scale goes through
+// shared memory to the rest of the CTA.
+template <int G>
+__global__ void __launch_bounds__(64 * G) k_fl_next(LargeArgs a, int st) {
+    __shared__ float s_rh[32];
+    const SegPos q = seg_pos<G>(a);
+    const float *a1 = acc_at(a, st, 0, q.tile);
+    const float *a2 = acc_at(a, st, 1, q.tile);
+    const int t = threadIdx.x;
+    if (t < 32) {
+        float rh = 0.f;
+        if (t < a.k) {
+            float H[NV][MS];
+            int sdim;
+            bool active;
+            replay(a, q.tile, t, st, H, sdim, active);
+            const bool was_active = active;
+            float h[MS], cc[NV];
 #pragma unroll
             for (int i = 0; i < MS; ++i) {
-                vq[i] = (i <= st) ? a.V[i * vs + o] : 0.f;
-                x = fmaf(-h[i], vq[i], x);
+                h[i] = (i <= st) ? a1[i * 32 + t] : 0.f;
+                cc[i] = (i <= st) ? a2[i * 32 + t] : 0.f;
             }
-            w[o] = x;
-#pragma unroll
-            for (int i = 0; i < MS; ++i)
-                if (i <= st) v[i] = fmaf(vq[i], x, v[i]);
-            v[MS] = fmaf(x, x, v[MS]);
+            cc[MS] = a2[MS * 32 + t];
+            const float hs = hess_column(H, h, cc, st, sqrtf(a1[MS * 32 + t]), active, sdim);
+            rh = (was_active && active) ? 1.f / hs : 0.f;
         }
-    seg_sum_add<L>(v, st + 1, red, acc_at(a, st, 1, tile), a.k);
-}
-
-// v_{st+1} = (w1 - V c) / h_{st+1,st}, zero once the column has stopped
-template <int L>
-__global__ void __launch_bounds__(256) k_fl_next(LargeArgs a, int st) {
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    if (j >= a.k) return;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t vs = a.nl * a.k;
-    float H[NV][MS];
-    int sdim;
-    bool active;
-    replay(a, tile, j, st, H, sdim, active);
-    const bool was_active = active;
-    const float *a1 = acc_at(a, st, 0, tile);
-    const float *a2 = acc_at(a, st, 1, tile);
-    float h[MS], c[NV];
+        s_rh[t] = rh;
+    }
+    __syncthreads();
+    if (q.r >= q.n || 4 * q.g >= a.kp) return;
+    const int64_t vs = a.nl * a.kp;
+    const int64_t o = q.p * a.kp + 4 * q.g;
+    float4 x = ld4(a.V + MS * vs + o);
 #pragma unroll
     for (int i = 0; i < MS; ++i) {
-        h[i] = (i <= st) ? a1[i * 32 + j] : 0.f;
-        c[i] = (i <= st) ? a2[i * 32 + j] : 0.f;
+        if (i <= st) {
+            const float4 c = ld4(a2 + i * 32 + 4 * q.g);
+            x = fma4v(make_float4(-c.x, -c.y, -c.z, -c.w), ld4(a.V + i * vs + o), x);
+        }
     }
-    c[MS] = a2[MS * 32 + j];
-    const float hs = hess_column(H, h, c, st, sqrtf(a1[MS * 32 + j]), active, sdim);
-    const float rh = (was_active && active) ? 1.f / hs : 0.f;
-    const float *w = a.V + MS * vs;
-    float *vn = a.V + (st + 1) * vs;
-    for (int r = slot; r < n; r += RP) {
-        const int64_t o = (p0 + r) * a.k + j;
-        float x = w[o];
-#pragma unroll
-        for (int i = 0; i < MS; ++i)
-            if (i <= st) x = fmaf(-c[i], a.V[i * vs + o], x);
-        vn[o] = x * rh;
-    }
+    const float4 rh = ld4(s_rh + 4 * q.g);
+    st4(a.V + (st + 1) * vs + o, make_float4(x.x * rh.x, x.y * rh.y, x.z * rh.z, x.w * rh.w));
 }
 
-// x = V_s y with H_s y = beta e_1 (every thread of a column solves the same
-// small system from the same sums)
-template <int L, typename T>
-__global__ void __launch_bounds__(256) k_fl_finish(LargeArgs a, const double *theta, T *W) {
-    constexpr int RP = 256 / L;
-    const int j = threadIdx.x % L, slot = threadIdx.x / L;
-    if (j >= a.k) return;
-    const int tile = a.seg_t[blockIdx.x];
-    const int64_t p0 = a.seg_p0[blockIdx.x];
-    const int n = a.seg_n[blockIdx.x];
-    const int64_t row0 = a.l_t0[tile] + (p0 - a.l_base[tile]);
-    const int64_t vs = a.nl * a.k;
-    float H[NV][MS];
-    int sdim;
-    bool active;
-    replay(a, tile, j, a.steps, H, sdim, active);
-    const float beta = sqrtf(a.accb[static_cast<int64_t>(tile) * 32 + j]);
-    const float th = static_cast<float>(theta[j]);
-    float y[MS];
-    hess_solve(H, sdim, beta, 1e-3f * fmaxf(1.f, fabsf(th)), y);
-    for (int r = slot; r < n; r += RP) {
-        const int64_t o = (p0 + r) * a.k + j;
-        float x = 0.f;
+// x = V_s y with H_s y = beta e_1: one thread per column replays the tile's
+// history and solves the small system; y goes through shared memory.
+template <int G, typename T>
+__global__ void __launch_bounds__(64 * G) k_fl_finish(LargeArgs a, const double *theta, T *W) {
+    __shared__ __align__(16) float s_y[MS][32];
+    const SegPos q = seg_pos<G>(a);
+    const int t = threadIdx.x;
+    if (t < 32) {
+        float y[MS];
 #pragma unroll
-        for (int i = 0; i < MS; ++i)
-            if (i < sdim) x = fmaf(y[i], a.V[i * vs + o], x);
-        W[(row0 + r) * a.k + j] = static_cast<T>(beta > 0.f ? x : 0.f);
+        for (int i = 0; i < MS; ++i) y[i] = 0.f;
+        if (t < a.k) {
+            float H[NV][MS];
+            int sdim;
+            bool active;
+            replay(a, q.tile, t, a.steps, H, sdim, active);
+            const float beta = sqrtf(a.accb[static_cast<int64_t>(q.tile) * 32 + t]);
+            const float th = static_cast<float>(theta[t]);
+            hess_solve(H, sdim, beta, 1e-3f * fmaxf(1.f, fabsf(th)), y);
+            if (!(beta > 0.f)) {
+#pragma unroll
+                for (int i = 0; i < MS; ++i) y[i] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MS; ++i) s_y[i][t] = y[i];
     }
+    __syncthreads();
+    if (q.r >= q.n || 4 * q.g >= a.kp) return;
+    const int64_t vs = a.nl * a.kp;
+    const int64_t row = a.l_t0[q.tile] + (q.p - a.l_base[q.tile]);
+    const int64_t o = q.p * a.kp + 4 * q.g;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < MS; ++i)
+        if (i < a.steps) x = fma4v(ld4(&s_y[i][4 * q.g]), ld4(a.V + i * vs + o), x);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (4 * q.g + c < a.k) W[row * a.k + 4 * q.g + c] = static_cast<T>(comp(x, c));
 }
 
 // ---------------------------------------------------------------- set-up
@@ -663,14 +719,14 @@ cudaError_t fom_setup_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t 
     }
     F.large_rows = nl;
     cudaError_t e = cudaSuccess;
-    auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+    auto up_ = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
         cudaError_t r = dev_alloc(h, dst, std::max<size_t>(bytes, 16));
         if (r == cudaSuccess && bytes) r = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
         return r;
     };
     if (F.n_small) {
-        e = up(reinterpret_cast<void **>(&F.s_t0), s_t0.data(), sizeof(int64_t) * F.n_small);
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.s_m), s_m.data(), sizeof(int32_t) * F.n_small);
+        e = up_(reinterpret_cast<void **>(&F.s_t0), s_t0.data(), sizeof(int64_t) * F.n_small);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.s_m), s_m.data(), sizeof(int32_t) * F.n_small);
         if (e == cudaSuccess) e = dev_alloc(h, reinterpret_cast<void **>(&F.A), sizeof(float) * F.n_small * BS * BS);
         if (e != cudaSuccess) return e;
         k_fom_dense<VT><<<static_cast<unsigned>(F.n_small), 256, 0, s>>>(F.s_t0, F.s_m, row_ptr, col, val, F.A);
@@ -678,9 +734,9 @@ cudaError_t fom_setup_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t 
         if (e != cudaSuccess) return e;
     }
     if (F.n_large) {
-        e = up(reinterpret_cast<void **>(&F.l_t0), l_t0.data(), sizeof(int64_t) * F.n_large);
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.l_m), l_m.data(), sizeof(int32_t) * F.n_large);
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.l_base), l_base.data(), sizeof(int64_t) * F.n_large);
+        e = up_(reinterpret_cast<void **>(&F.l_t0), l_t0.data(), sizeof(int64_t) * F.n_large);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.l_m), l_m.data(), sizeof(int32_t) * F.n_large);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.l_base), l_base.data(), sizeof(int64_t) * F.n_large);
         if (e != cudaSuccess) return e;
         int64_t *d_cnt = nullptr;
         e = cudaMallocAsync(&d_cnt, sizeof(int64_t) * nl, s);
@@ -695,13 +751,72 @@ cudaError_t fom_setup_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t 
         if (e != cudaSuccess) return e;
         rp[0] = 0;
         for (int64_t p = 0; p < nl; ++p) rp[p + 1] = rp[p] + cnt[p];
-        F.large_nnz = rp[nl];
-        e = up(reinterpret_cast<void **>(&F.rp), rp.data(), sizeof(int64_t) * (nl + 1));
-        if (e == cudaSuccess) e = dev_alloc(h, reinterpret_cast<void **>(&F.col), sizeof(int32_t) * std::max<int64_t>(F.large_nnz, 4));
-        if (e == cudaSuccess) e = dev_alloc(h, reinterpret_cast<void **>(&F.val), sizeof(float) * std::max<int64_t>(F.large_nnz, 4));
+        const int64_t lnnz = rp[nl];
+        // the tiles' lower triangles (local columns) into temporaries ...
+        int64_t *d_rp = nullptr;
+        int32_t *d_col = nullptr;
+        float *d_val = nullptr;
+        e = cudaMallocAsync(&d_rp, sizeof(int64_t) * (nl + 1), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_col, sizeof(int32_t) * std::max<int64_t>(lnnz, 4), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_val, sizeof(float) * std::max<int64_t>(lnnz, 4), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp.data(), sizeof(int64_t) * (nl + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            k_fom_rows<true, VT><<<static_cast<unsigned>(F.n_large), 256, 0, s>>>(
+                F.l_t0, F.l_m, F.l_base, row_ptr, col, val, nullptr, d_rp, d_col, d_val);
+            e = cudaGetLastError();
+        }
+        std::vector<int32_t> lc(lnnz);
+        std::vector<float> lv(lnnz);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lc.data(), d_col, sizeof(int32_t) * lnnz, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lv.data(), d_val, sizeof(float) * lnnz, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(d_rp, s);
+        cudaFreeAsync(d_col, s);
+        cudaFreeAsync(d_val, s);
+        if (e != cudaSuccess) return e;
+        // ... expanded on the host to both triangles: row c = its stored
+        // entries (columns <= c, ascending) followed by the transposes of
+        // the entries (r, c), r > c, in increasing r (so rows stay sorted)
+        std::vector<int64_t> up(nl, 0), frp(nl + 1, 0);
+        for (int64_t q = 0; q < F.n_large; ++q)
+            for (int64_t r = 0; r < l_m[q]; ++r) {
+                const int64_t p = l_base[q] + r;
+                for (int64_t e2 = rp[p]; e2 < rp[p + 1]; ++e2)
+                    if (lc[e2] < r) ++up[l_base[q] + lc[e2]];
+            }
+        for (int64_t p = 0; p < nl; ++p) frp[p + 1] = frp[p] + cnt[p] + up[p];
+        F.large_nnz = frp[nl];
+        std::vector<int32_t> fc(F.large_nnz);
+        std::vector<float> fv(F.large_nnz);
+        std::vector<int64_t> cur(nl);
+        for (int64_t p = 0; p < nl; ++p) {
+            cur[p] = frp[p];
+            for (int64_t e2 = rp[p]; e2 < rp[p + 1]; ++e2, ++cur[p]) {
+                fc[cur[p]] = lc[e2];
+                fv[cur[p]] = lv[e2];
+            }
+        }
+        for (int64_t q = 0; q < F.n_large; ++q)
+            for (int64_t r = 0; r < l_m[q]; ++r) {
+                const int64_t p = l_base[q] + r;
+                for (int64_t e2 = rp[p]; e2 < rp[p + 1]; ++e2)
+                    if (lc[e2] < r) {
+                        const int64_t t = l_base[q] + lc[e2];
+                        fc[cur[t]] = static_cast<int32_t>(r);
+                        fv[cur[t]] = lv[e2];
+                        ++cur[t];
+                    }
+            }
+        e = up_(reinterpret_cast<void **>(&F.rp), frp.data(), sizeof(int64_t) * (nl + 1));
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.col), fc.data(), sizeof(int32_t) * F.large_nnz);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.val), fv.data(), sizeof(float) * F.large_nnz);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host arrays above die with this scope
         F.scr_k = h->params.k;
+        const int64_t kp_max = (F.scr_k + 3) & ~3;
         if (e == cudaSuccess)
-            e = dev_alloc(h, reinterpret_cast<void **>(&F.scr), sizeof(float) * (MS + 1) * nl * F.scr_k);
+            e = dev_alloc(h, reinterpret_cast<void **>(&F.scr), sizeof(float) * (MS + 1) * nl * kp_max);
+        // the padding columns of the basis stay zero
+        if (e == cudaSuccess) e = cudaMemsetAsync(F.scr, 0, sizeof(float) * (MS + 1) * nl * kp_max, s);
         // 64-row segments inside each large tile
         std::vector<int64_t> seg_p0;
         std::vector<int32_t> seg_n, seg_t;
@@ -712,15 +827,11 @@ cudaError_t fom_setup_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t 
                 seg_t.push_back(static_cast<int32_t>(q));
             }
         F.n_seg = static_cast<int64_t>(seg_p0.size());
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.seg_p0), seg_p0.data(), sizeof(int64_t) * F.n_seg);
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.seg_n), seg_n.data(), sizeof(int32_t) * F.n_seg);
-        if (e == cudaSuccess) e = up(reinterpret_cast<void **>(&F.seg_t), seg_t.data(), sizeof(int32_t) * F.n_seg);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.seg_p0), seg_p0.data(), sizeof(int64_t) * F.n_seg);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.seg_n), seg_n.data(), sizeof(int32_t) * F.n_seg);
+        if (e == cudaSuccess) e = up_(reinterpret_cast<void **>(&F.seg_t), seg_t.data(), sizeof(int32_t) * F.n_seg);
         if (e == cudaSuccess)
             e = dev_alloc(h, reinterpret_cast<void **>(&F.acc), sizeof(float) * (MS * 2 + 1) * F.n_large * NV * 32);
-        if (e != cudaSuccess) return e;
-        k_fom_rows<true, VT><<<static_cast<unsigned>(F.n_large), 256, 0, s>>>(
-            F.l_t0, F.l_m, F.l_base, row_ptr, col, val, nullptr, F.rp, F.col, F.val);
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     e = cudaStreamSynchronize(s);
@@ -744,6 +855,7 @@ cudaError_t fom_launch(const lobpcg_ctx *h, int k, int steps, const T *R, const 
         if (k > F.scr_k) return cudaErrorInvalidValue;
         LargeArgs a{};
         a.k = k;
+        a.kp = (k + 3) & ~3;
         a.steps = steps;
         a.nl = F.large_rows;
         a.nlt = F.n_large;
@@ -762,17 +874,17 @@ cudaError_t fom_launch(const lobpcg_ctx *h, int k, int steps, const T *R, const 
         cudaError_t e = cudaMemsetAsync(a.acc, 0, sizeof(float) * steps * 2 * F.n_large * NV * 32, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(a.accb, 0, sizeof(float) * F.n_large * 32, s);
         if (e != cudaSuccess) return e;
+        constexpr int G = L / 4;
         const unsigned g = static_cast<unsigned>(F.n_seg);
-        k_fl_norm<L, T><<<g, 256, 0, s>>>(a, R);
-        k_fl_start<L, T><<<g, 256, 0, s>>>(a, R);
+        k_fl_norm<G, T><<<g, 64 * G, 0, s>>>(a, R);
+        k_fl_start<G, T><<<g, 64 * G, 0, s>>>(a, R);
         for (int st = 0; st < steps; ++st) {
-            k_fl_gather<L><<<g, 256, 0, s>>>(a, st, theta);
-            k_fl_scatter<L><<<g, 256, 0, s>>>(a, st);
-            k_fl_dots1<L><<<g, 256, 0, s>>>(a, st);
-            k_fl_dots2<L><<<g, 256, 0, s>>>(a, st);
-            if (st + 1 < steps) k_fl_next<L><<<g, 256, 0, s>>>(a, st);
+            k_fl_matvec<G><<<g, 64 * G, 0, s>>>(a, st, theta);
+            k_fl_dots1<G><<<g, 64 * G, 0, s>>>(a, st);
+            k_fl_dots2<G><<<g, 64 * G, 0, s>>>(a, st);
+            if (st + 1 < steps) k_fl_next<G><<<g, 64 * G, 0, s>>>(a, st);
         }
-        k_fl_finish<L, T><<<g, 256, 0, s>>>(a, theta, W);
+        k_fl_finish<G, T><<<g, 64 * G, 0, s>>>(a, theta, W);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -56,8 +56,8 @@ struct Tiled {
 // Diagonal tiles of the FOM preconditioner (fom.cu).  Small tiles (<= 64
 // rows): dense FP32 64 x 64 blocks, both triangles, zero outside the m x m
 // corner, one per small tile in s_t0 order.  Large tiles (> 64 rows), in
-// decreasing size: the lower triangle of each tile as a CSR over the rows
-// of the large tiles packed one after another (tile q starts at packed row
+// decreasing size: each tile as a CSR of both triangles over the rows of
+// the large tiles packed one after another (tile q starts at packed row
 // l_base[q]), local column indices, cut into segments of <= 64 rows inside
 // one tile; scr holds the Krylov basis and work vector of every large-tile
 // row (7 blocks of large_rows x scr_k floats), acc the per-tile sums.
