@@ -258,14 +258,16 @@ def fom_report(pkg, A, p, stream, sm_mhz: float) -> dict:
     return out
 
 
-def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var", "mlp")):
+def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var", "mlp", "davidson_diag")):
     """Time-to-solution (relative residual 1e-6, nev pairs) from a host X0,
     through lobpcg_solve; create (matrix tiling, preconditioner set-up) is
     timed separately.  The learned form ("mlp") is first trained on pairs
     harvested from 20 block-Jacobi iterations from the same X0 (about 1M
     pairs, 5 epochs, Adam lr 1e-3): its training time is reported on its own
     and added in.  "fom" runs 4 FOM steps per 64-row tile, "fom_var" the same
-    on a seeded partition into 5..6000-row tiles (synth.tile_partition)."""
+    on a seeded partition into 5..6000-row tiles (synth.tile_partition);
+    "davidson_diag" is block Davidson (lobpcg_davidson, basis of 6 blocks)
+    with the diagonal form on the same SpMM."""
     import torch
     out = {}
     X0 = synth.initial_guess(A, p["k"], seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
@@ -273,7 +275,8 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         extra = {"fom_tile_ptr": synth.tile_partition(A.n, p["seed"])} if pc == "fom_var" else {}
-        h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc.replace("_var", ""),
+        pcond = pc.replace("_var", "").replace("davidson_", "")
+        h = pkg.from_csr(A, k=p["k"], nev=p["nev"], tol=1e-6, maxiter=1000, precond=pcond,
                          polish_fp64=1, stream=stream, seed=p["seed"], **extra)
         torch.cuda.synchronize()
         t_create = time.perf_counter() - t0
@@ -285,7 +288,7 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
                      "held_out_mse": [round(float(v), 5) for v in hist]}
         t0 = time.perf_counter()
         try:
-            X, ev, rs, st = h.solve(X0)
+            X, ev, rs, st = h.davidson(X0) if pc.startswith("davidson") else h.solve(X0)
             ok = True
         except pkg.LobpcgError as e:
             X, ev, rs, st = e.result

@@ -270,6 +270,27 @@ LOBPCG_API lobpcg_status lobpcg_rayleigh_ritz_noalloc(lobpcg_t h, const float *S
 LOBPCG_API lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, lobpcg_stats *st);
 
 /*
+ * The k leftmost eigenpairs of H by block Davidson on the same SpMM,
+ * preconditioner (params.precond), tolerance and limits: the paper notes
+ * (Section 1) that its techniques carry over to other block eigensolvers.
+ * Each iteration takes the k leftmost Ritz pairs of (V^T H V, V^T V) on the
+ * orthonormal basis V, and, unless the nev leftmost have converged, appends
+ * the preconditioned residuals orthonormalised against V (one SpMM per
+ * iteration); when V holds max_blocks blocks it restarts from the k Ritz
+ * vectors.  float32 vectors; when the residual stalls above tol and
+ * params.polish_fp64 is set, the same iteration continues in float64 (with
+ * the float64 SpMM).  Convergence is confirmed with an explicit SpMM.
+ *   X          : as lobpcg_solve (in: X0, out: Ritz vectors; device or host)
+ *   max_blocks : basis limit in blocks of k columns, 2 .. min(6, 96 / k)
+ *   evals, resid, stats : as lobpcg_solve
+ * The first call allocates 2 max_blocks blocks of n x k float32 (and of
+ * float64 with polish_fp64) for the life of the handle; a later call may not
+ * ask for more blocks (ERR_ARG).  Errors as lobpcg_solve.
+ */
+LOBPCG_API lobpcg_status lobpcg_davidson(lobpcg_t h, float *X, int32_t max_blocks, double *evals, double *resid,
+                                         lobpcg_stats *stats);
+
+/*
  * Run exactly `steps` float32 LOBPCG iterations (Algorithm 1, lines 6-12,
  * without the exit test; the residual norms are still formed and read back
  * each iteration as in lobpcg_solve).  X0 (n x k float32, device or host)

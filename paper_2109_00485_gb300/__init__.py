@@ -98,6 +98,8 @@ def load():
     L.lobpcg_rayleigh_ritz_noalloc.restype = st
     L.lobpcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Stats)]
     L.lobpcg_solve.restype = st
+    L.lobpcg_davidson.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(_Stats)]
+    L.lobpcg_davidson.restype = st
     L.lobpcg_iterate.argtypes = [vp, vp, i32, vp, ctypes.POINTER(_Stats)]
     L.lobpcg_iterate.restype = st
     L.lobpcg_get_x_f64.argtypes = [vp, vp]
@@ -228,6 +230,18 @@ class Handle:
         """Run LOBPCG from X0 (float32 n x k: CUDA tensor, or host numpy / CPU
         tensor).  Returns (X, evals, resid, stats) with X of the same kind;
         raises LobpcgError on failure (NOT_CONVERGED carries .result)."""
+        return self._run(X0, lambda X, ev, rs, stats: load().lobpcg_solve(
+            self._h, _ptr(X), ev.ctypes.data, rs.ctypes.data, ctypes.byref(stats)))
+
+    def lobpcg_davidson(self, X0, max_blocks: int = 0):
+        """Block Davidson from X0 on the same SpMM and preconditioner (basis
+        of at most max_blocks blocks of k columns; 0: min(6, 96 // k)).
+        Returns and raises as lobpcg_solve."""
+        mb = int(max_blocks) if max_blocks else min(6, 96 // self.params.k)
+        return self._run(X0, lambda X, ev, rs, stats: load().lobpcg_davidson(
+            self._h, _ptr(X), mb, ev.ctypes.data, rs.ctypes.data, ctypes.byref(stats)))
+
+    def _run(self, X0, call):
         k = self.params.k
         nev = self.params.nev
         if isinstance(X0, np.ndarray):
@@ -241,7 +255,7 @@ class Handle:
         ev = np.zeros(nev)
         rs = np.zeros(nev)
         stats = _Stats()
-        status = load().lobpcg_solve(self._h, _ptr(X), ev.ctypes.data, rs.ctypes.data, ctypes.byref(stats))
+        status = call(X, ev, rs, stats)
         result = (X, ev, rs, {f: getattr(stats, f) for f, _ in _Stats._fields_})
         if status != LOBPCG_OK:
             err = LobpcgError(status, self.lobpcg_last_error())
@@ -342,6 +356,7 @@ class Handle:
     rayleigh_ritz = lobpcg_rayleigh_ritz
     rayleigh_ritz_noalloc = lobpcg_rayleigh_ritz_noalloc
     solve = lobpcg_solve
+    davidson = lobpcg_davidson
     iterate = lobpcg_iterate
     get_x_f64 = lobpcg_get_x_f64
     sync = lobpcg_sync

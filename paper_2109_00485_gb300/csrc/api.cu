@@ -305,6 +305,21 @@ lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, l
     return LOBPCG_OK;
 }
 
+lobpcg_status lobpcg_davidson(lobpcg_t h, float *X, int32_t max_blocks, double *evals, double *resid,
+                              lobpcg_stats *st) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (!X) return fail(h, LOBPCG_ERR_ARG, "X is NULL");
+    if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
+    if (max_blocks < 2 || max_blocks > 6 || max_blocks * h->params.k > 96)
+        return fail(h, LOBPCG_ERR_ARG, "max_blocks must be in [2, min(6, 96 / k)]");
+    if (h->params.precond == 3 && !h->mlp.ready)
+        return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned preconditioner has no weights (train or set them first)");
+    std::string err;
+    lobpcg_status s = davidson(h, X, is_host_ptr(X), max_blocks, evals, resid, st, err);
+    if (s != LOBPCG_OK) return fail(h, s, err);
+    return LOBPCG_OK;
+}
+
 lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double *theta, lobpcg_stats *st) {
     if (!h) return LOBPCG_ERR_ARG;
     if (steps < 0) return fail(h, LOBPCG_ERR_ARG, "steps must be >= 0");

@@ -10,6 +10,7 @@
 namespace lobpcg {
 
 struct SolverState;
+struct DavState;
 
 // One 16-byte record per chunk (see Tiled).
 struct __align__(16) ChunkRec {
@@ -103,6 +104,7 @@ struct lobpcg_ctx {
     float *bj_lam = nullptr;
     lobpcg::FomTiles fom;        // FOM preconditioner tiles (fom.cu)
     lobpcg::SolverState *solver = nullptr;  // workspaces of lobpcg_solve (solver.cu)
+    lobpcg::DavState *dav = nullptr;        // workspaces of lobpcg_davidson (solver.cu), made on first use
     lobpcg::Mlp mlp;                         // learned tile preconditioner (mlp.cu)
     std::string last_error;
 };
@@ -126,6 +128,8 @@ void solver_release(lobpcg_ctx *h);
 lobpcg_status solve(lobpcg_ctx *h, float *X, bool x_on_host, double *evals, double *resid, lobpcg_stats *st,
                     std::string &err);
 cudaError_t copy_x_f64(lobpcg_ctx *h, double *out);
+lobpcg_status davidson(lobpcg_ctx *h, float *X, bool x_on_host, int max_blocks, double *evals, double *resid,
+                       lobpcg_stats *st, std::string &err);
 lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps, double *theta_out,
                       lobpcg_stats *st, std::string &err, int harvest = 0);
 

@@ -56,6 +56,26 @@ struct SolverState {
     bool ev_pending = false;
 };
 
+// Block Davidson workspace (lobpcg_davidson): up to nbmax blocks of the
+// basis V and of HV, float32 and (for the float64 phase) float64.
+struct DavState {
+    int k = 0, nbmax = 0;
+    float *V32[6] = {}, *HV32[6] = {};
+    double *V64[6] = {}, *HV64[6] = {};
+    double *G = nullptr;    // [V^T HV] then [V^T V], two m x m blocks (m <= 96)
+    double *C = nullptr;    // m x k Ritz coefficients
+    double *B = nullptr;    // m x k: V^T W
+    double *Cp = nullptr;   // (k + m) x k: [I; -B]
+};
+
+// Cp = [I; -B] ((k + m) x k): W - V B = [W V] Cp
+__global__ void k_proj_coef_m(int k, int m, const double *B, double *Cp) {
+    for (int e = threadIdx.x; e < (k + m) * k; e += blockDim.x) {
+        const int r = e / k, j = e % k;
+        Cp[e] = (r < k) ? (r == j ? 1.0 : 0.0) : -B[(r - k) * k + j];
+    }
+}
+
 __global__ void k_proj_coef(int k, const double *B, double *Cp) {
     // Cp = [I; -B]  (2k x k): W - X B = [W X] Cp
     for (int e = threadIdx.x; e < 2 * k * k; e += blockDim.x) {
@@ -581,6 +601,8 @@ cudaError_t solver_setup(lobpcg_ctx *h) {
 }
 
 void solver_release(lobpcg_ctx *h) {
+    delete h->dav;
+    h->dav = nullptr;
     if (!h->solver) return;
     if (h->solver->h_buf) cudaFreeHost(h->solver->h_buf);
     if (h->solver->ev0) cudaEventDestroy(h->solver->ev0);
@@ -705,6 +727,261 @@ cudaError_t copy_x_f64(lobpcg_ctx *h, double *out) {
     cudaError_t e = cudaMemcpyAsync(out, s->d.X, sizeof(double) * h->T.n * s->k, cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e;
+}
+
+}  // namespace lobpcg
+
+// ---------------------------------------------------------------- block Davidson
+// The same SpMM, preconditioners, Gram, combine and Rayleigh-Ritz kernels
+// inside block (generalised) Davidson: a growing orthonormal basis V of at
+// most nbmax blocks, the k leftmost Ritz pairs of (V^T H V, V^T V) each
+// iteration, the preconditioned residuals orthonormalised against V and
+// appended (one SpMM per iteration), and a restart to the Ritz vectors when
+// V is full.  float32 first; when its residual stalls above tol and
+// params.polish_fp64 is set, the same iteration continues in float64.
+
+namespace {
+
+// W <- W - V (V^T W), then Cholesky-QR (SVQB on failure); twice.
+template <typename T>
+cudaError_t dav_orth(lobpcg_ctx *h, SolverState *s, DavState *D, T *const *V, int nb, T *W) {
+    const int k = s->k, m = nb * k;
+    const int64_t n = h->T.n;
+    GemmBlocks<T> av{}, aw{}, awv{};
+    for (int q = 0; q < nb; ++q) {
+        av.p[q] = V[q];
+        awv.p[q + 1] = V[q];
+    }
+    aw.p[0] = W;
+    awv.p[0] = W;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (nb > 0) {
+            CK(launch_gram<T>(n, k, nb, av, 1, aw, D->B, h->num_sms, h->stream, h->d_err));   // B = V^T W
+            k_proj_coef_m<<<1, 256, 0, h->stream>>>(k, m, D->B, D->Cp);
+            CK(cudaGetLastError());
+            CombineOut<T> o1{};
+            o1.z[0] = W; o1.C[0] = D->Cp; o1.c0[0] = 0; o1.norm_of = -1; o1.Cf = s->Cf;
+            CK(launch_combine<T>(n, k, nb + 1, awv, 1, o1, nullptr, h->num_sms, h->stream));   // W -= V B
+        }
+        CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream, h->d_err));         // W^T W
+        CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
+        CombineOut<T> o2{};
+        o2.z[0] = W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1; o2.Cf = s->Cf;
+        CK(launch_combine<T>(n, k, 1, aw, 1, o2, nullptr, h->num_sms, h->stream));              // W <- W T
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+T **dav_v(DavState *D);
+template <>
+float **dav_v<float>(DavState *D) { return D->V32; }
+template <>
+double **dav_v<double>(DavState *D) { return D->V64; }
+template <typename T>
+T **dav_hv(DavState *D);
+template <>
+float **dav_hv<float>(DavState *D) { return D->HV32; }
+template <>
+double **dav_hv<double>(DavState *D) { return D->HV64; }
+
+template <typename T>
+cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters, bool stop_on_stagnation,
+                      PhaseResult &res, lobpcg_stats *st, lobpcg_status &status) {
+    const int k = s->k, nev = h->params.nev;
+    const int64_t n = h->T.n;
+    const double tol = h->params.tol;
+    const size_t blk = sizeof(T) * n * k;
+    Blocks<T> &b = blocks_of<T>(s);
+    T **V = dav_v<T>(D), **HV = dav_hv<T>(D);
+    const int pmode = effective_precond<T>(h);
+    const char *tag = std::is_same<T, float>::value ? "dav32" : "dav64";
+    status = LOBPCG_OK;
+    // V_0: an orthonormal basis of X
+    CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
+    CK(dav_orth<T>(h, s, D, V, 0, V[0]));
+    CK(spmm_T<T>(h, V[0], HV[0], k));
+    int nb = 1, restarts = 0, since_best = 0;
+    double best = INFINITY;
+    std::vector<double> rho, theta;
+    while (true) {
+        const int m = nb * k;
+        GemmBlocks<T> av{}, ahv{};
+        for (int q = 0; q < nb; ++q) {
+            av.p[q] = V[q];
+            ahv.p[q] = HV[q];
+        }
+        CK(launch_gram<T>(n, k, nb, av, nb, ahv, D->G, h->num_sms, h->stream, h->d_err));           // V^T HV
+        CK(launch_gram<T>(n, k, nb, av, nb, av, D->G + m * m, h->num_sms, h->stream, h->d_err));    // V^T V
+        CK(launch_rayleigh_ritz(m, k, m, D->G, D->G + m * m, m, nullptr, D->C, s->theta, s->status, h->stream));
+        CombineOut<T> ox{}, oh{};
+        ox.z[0] = b.X; ox.C[0] = D->C; ox.c0[0] = 0; ox.norm_of = -1; ox.Cf = s->Cf;
+        oh.z[0] = b.HX; oh.C[0] = D->C; oh.c0[0] = 0; oh.norm_of = -1; oh.Cf = s->Cf;
+        CK(launch_combine<T>(n, k, nb, av, 1, ox, nullptr, h->num_sms, h->stream));     // X = V C
+        CK(launch_combine<T>(n, k, nb, ahv, 1, oh, nullptr, h->num_sms, h->stream));    // HX = HV C
+        CK(launch_resid<T>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
+                           h->stream));
+        int rr_st = 0, orth_st = 0;
+        CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
+        trace(tag, res.iters, rho, theta, nev, rr_st);
+        if (rr_st == 2) {
+            status = LOBPCG_ERR_BREAKDOWN;
+            break;
+        }
+        if (orth_st == 1 && st) st->svqb_used++;
+        bool finite = true;
+        for (int j = 0; j < k; ++j) finite = finite && std::isfinite(rho[j]) && std::isfinite(theta[j]);
+        if (!finite) {
+            status = LOBPCG_ERR_NONFINITE;
+            break;
+        }
+        double worst = 0.0;
+        for (int j = 0; j < nev; ++j) worst = std::max(worst, rho[j]);
+        if (worst <= tol) {
+            // explicit re-check: H X from a fresh SpMM (into HW as scratch)
+            CK(spmm_T<T>(h, b.X, b.HW, k));
+            CK(launch_resid<T>(n, k, b.X, b.HW, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms,
+                               h->num_sms, h->stream));
+            CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
+            double worst_e = 0.0;
+            for (int j = 0; j < nev; ++j) worst_e = std::max(worst_e, rho[j]);
+            trace("check", res.iters, rho, theta, nev, 0);
+            if (worst_e <= tol || restarts >= 5) {
+                res.converged = worst_e <= tol;
+                break;
+            }
+            ++restarts;
+            if (st) st->explicit_restarts++;
+            // continue from the Ritz vectors and their explicit product
+            CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
+            CK(cudaMemcpyAsync(HV[0], b.HW, blk, cudaMemcpyDeviceToDevice, h->stream));
+            nb = 1;
+            continue;
+        }
+        // a float32 run hands over once its residual stalls (15 iterations
+        // without a 0.7x gain) or grows 4x above a best below 1e-3
+        if (worst < 0.7 * best) {
+            best = worst;
+            since_best = 0;
+        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best))) {
+            res.stagnated = true;
+            break;
+        }
+        if (res.iters >= max_iters) break;
+        ++res.iters;
+        if (pmode >= 2) CK(precond_apply<T>(h, pmode, k, b.W, s->theta, b.W, h->stream));
+        if (nb == D->nbmax) {   // restart with the Ritz vectors
+            CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
+            CK(cudaMemcpyAsync(HV[0], b.HX, blk, cudaMemcpyDeviceToDevice, h->stream));
+            nb = 1;
+        }
+        CK(cudaMemcpyAsync(V[nb], b.W, blk, cudaMemcpyDeviceToDevice, h->stream));
+        CK(dav_orth<T>(h, s, D, V, nb, V[nb]));
+        CK(timed_spmm<T>(h, s, V[nb], HV[nb], k));   // the one SpMM per iteration
+        ++nb;
+    }
+    res.rho = rho;
+    res.theta = theta;
+    return cudaSuccess;
+}
+
+cudaError_t dav_setup(lobpcg_ctx *h, int nbmax) {
+    DavState *D = new DavState();
+    h->dav = D;
+    const int k = h->params.k;
+    const int64_t n = h->T.n;
+    D->k = k;
+    D->nbmax = nbmax;
+    const int mmax = nbmax * k;
+    for (int q = 0; q < nbmax; ++q) {
+        CK(dev_alloc(h, reinterpret_cast<void **>(&D->V32[q]), sizeof(float) * n * k));
+        CK(dev_alloc(h, reinterpret_cast<void **>(&D->HV32[q]), sizeof(float) * n * k));
+        if (h->params.polish_fp64) {
+            CK(dev_alloc(h, reinterpret_cast<void **>(&D->V64[q]), sizeof(double) * n * k));
+            CK(dev_alloc(h, reinterpret_cast<void **>(&D->HV64[q]), sizeof(double) * n * k));
+        }
+    }
+    CK(dev_alloc(h, reinterpret_cast<void **>(&D->G), sizeof(double) * 2 * mmax * mmax));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&D->C), sizeof(double) * mmax * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&D->B), sizeof(double) * mmax * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&D->Cp), sizeof(double) * (mmax + k) * k));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace lobpcg {
+
+lobpcg_status davidson(lobpcg_ctx *h, float *Xio, bool x_on_host, int max_blocks, double *evals, double *resid,
+                       lobpcg_stats *st, std::string &err) {
+    SolverState *s = h->solver;
+    const int k = s->k, nev = h->params.nev;
+    const int64_t n = h->T.n;
+    const size_t bytes32 = sizeof(float) * n * k;
+    auto t0 = std::chrono::steady_clock::now();
+    if (st) std::memset(st, 0, sizeof(*st));
+    auto cuda_err = [&](const char *where, cudaError_t e) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return LOBPCG_ERR_CUDA;
+    };
+    if (!h->dav) {
+        cudaError_t e = dav_setup(h, max_blocks);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LOBPCG_ERR_OOM : cuda_err("davidson setup", e);
+    } else if (max_blocks > h->dav->nbmax) {
+        err = "max_blocks larger than at the first lobpcg_davidson call on this handle";
+        return LOBPCG_ERR_ARG;
+    }
+    DavState *D = h->dav;
+    const int saved = D->nbmax;
+    D->nbmax = max_blocks;
+    cudaError_t e = cudaMemcpyAsync(s->f.X, Xio, bytes32, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_err("davidson", e);
+    PhaseResult r32;
+    lobpcg_status status = LOBPCG_OK;
+    const bool polish = h->params.polish_fp64 && s->d.X && D->V64[0];
+    e = dav_phase<float>(h, s, D, h->params.maxiter, polish, r32, st, status);
+    if (e != cudaSuccess) { D->nbmax = saved; return cuda_err("davidson (fp32)", e); }
+    PhaseResult final = r32;
+    int iters64 = 0;
+    bool used64 = false;
+    const int nb = std::max(1, std::min<int>(h->num_sms * 8, static_cast<int>((n * k + 255) / 256)));
+    if (status == LOBPCG_OK && !r32.converged && polish) {
+        k_convert<float, double><<<nb, 256, 0, h->stream>>>(n * k, s->f.X, s->d.X);
+        PhaseResult r64;
+        e = dav_phase<double>(h, s, D, std::max(0, h->params.maxiter - r32.iters), false, r64, st, status);
+        if (e != cudaSuccess) { D->nbmax = saved; return cuda_err("davidson (fp64)", e); }
+        iters64 = r64.iters;
+        final = r64;
+        used64 = true;
+        k_convert<double, float><<<nb, 256, 0, h->stream>>>(n * k, s->d.X, s->f.X);
+    } else if (s->d.X) {
+        k_convert<float, double><<<nb, 256, 0, h->stream>>>(n * k, s->f.X, s->d.X);
+    }
+    D->nbmax = saved;
+    e = cudaMemcpyAsync(Xio, s->f.X, bytes32, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_err("davidson", e);
+    for (int j = 0; j < nev && j < static_cast<int>(final.theta.size()); ++j) {
+        if (evals) evals[j] = final.theta[j];
+        if (resid) resid[j] = final.rho[j];
+    }
+    if (st) {
+        st->iters = r32.iters + iters64;
+        st->iters_fp64 = iters64;
+        st->used_fp64 = used64 ? 1 : 0;
+        st->converged = final.converged ? 1 : 0;
+        st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != LOBPCG_OK) {
+        err = status == LOBPCG_ERR_BREAKDOWN ? "Rayleigh-Ritz breakdown" : "non-finite residual";
+        return status;
+    }
+    if (!final.converged) {
+        err = "maxiter reached before the residual tolerance";
+        return LOBPCG_ERR_NOT_CONVERGED;
+    }
+    return LOBPCG_OK;
 }
 
 }  // namespace lobpcg
