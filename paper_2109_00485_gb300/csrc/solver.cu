@@ -54,6 +54,9 @@ struct SolverState {
     bool ready32 = false;        // lobpcg_iterate: state initialised
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the SpMM of an iteration
     bool ev_pending = false;
+    cudaGraphExec_t gpre = nullptr, gpost = nullptr;   // float32 iteration with P, before / after the SpMM
+    int graph_pmode = -1;                              // preconditioner the graphs were captured with
+    bool graph_failed = false;                         // capture failed once: launch directly
 };
 
 // Block Davidson workspace (lobpcg_davidson): up to nbmax blocks of the
@@ -254,58 +257,131 @@ int effective_precond(const lobpcg_ctx *h) {
     return (std::is_same<T, double>::value && p == 3) ? 1 : p;
 }
 
+// Before the SpMM: preconditioner (the diagonal one was applied inside the
+// residual kernel) and the two orthonormalisation passes of W.
 template <typename T>
-cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP, int pmode, int harvest_iter = -1) {
+cudaError_t body_pre(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, int pmode, int harvest_iter) {
     const int k = s->k;
     const int64_t n = h->T.n;
-        // preconditioner (the diagonal one was applied inside the residual kernel)
-        if (pmode == 2) {
-            if constexpr (std::is_same<T, float>::value) {
-                if (harvest_iter >= 0) {   // exact tile solves into HW, harvest (R, solve) pairs, then W = HW
-                    CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.HW, h->stream));
-                    CK(mlp_harvest(h, k, b.W, b.HW, s->theta, harvest_iter));
-                    CK(cudaMemcpyAsync(b.W, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
-                } else {
-                    CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
-                }
+    if (pmode == 2) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (harvest_iter >= 0) {   // exact tile solves into HW, harvest (R, solve) pairs, then W = HW
+                CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.HW, h->stream));
+                CK(mlp_harvest(h, k, b.W, b.HW, s->theta, harvest_iter));
+                CK(cudaMemcpyAsync(b.W, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             } else {
                 CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
             }
+        } else {
+            CK(precond_apply<T>(h, 2, k, b.W, s->theta, b.W, h->stream));
         }
-        if (pmode == 3 || pmode == 4) CK(precond_apply<T>(h, pmode, k, b.W, s->theta, b.W, h->stream));
-        // orthonormalise W against X and itself
-        CK(orth_pass<T>(h, s, b));
-        CK(orth_pass<T>(h, s, b));
-        // the one SpMM per iteration
-        CK(timed_spmm<T>(h, s, b.W, b.HW, k));
-        // Gram matrices of S = [X W P], HS = [HX HW HP]
-        const int na = hasP ? 3 : 2;
-        const int m = na * k;
-        GemmBlocks<T> aS{}, aHS{}, aB{};
-        aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
-        aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
-        for (int q = 0; q < na; ++q) {
-            aB.p[q] = aHS.p[q];
-            aB.p[na + q] = aS.p[q];
-        }
-        CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));   // [S^T HS | S^T S]
-        if (hasP) {
-            k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
-            CK(cudaGetLastError());
-        }
-        CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->G + m, 2 * m, hasP ? s->pscale : nullptr, s->C, s->theta,
-                                s->status, h->stream));
-        // X = S C, P = [W P] C_23 (with ||p_j||^2), HX = HS C, HP = [HW HP] C_23
-        CombineOut<T> ox{}, oh{};
-        ox.Cf = s->Cf;
-        oh.Cf = s->Cf;
-        ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0;
-        ox.z[1] = b.P; ox.C[1] = s->C + static_cast<int64_t>(k) * k; ox.c0[1] = k; ox.norm_of = 1;
-        oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0;
-        oh.z[1] = b.HP; oh.C[1] = s->C + static_cast<int64_t>(k) * k; oh.c0[1] = k; oh.norm_of = -1;
-        CK(launch_combine<T>(n, k, na, aS, 2, ox, s->colsqP, h->num_sms, h->stream));
-        CK(launch_combine<T>(n, k, na, aHS, 2, oh, nullptr, h->num_sms, h->stream));
+    }
+    if (pmode == 3 || pmode == 4) CK(precond_apply<T>(h, pmode, k, b.W, s->theta, b.W, h->stream));
+    // orthonormalise W against X and itself
+    CK(orth_pass<T>(h, s, b));
+    CK(orth_pass<T>(h, s, b));
     return cudaSuccess;
+}
+
+// After the SpMM: Gram matrices of S = [X W P], HS = [HX HW HP],
+// Rayleigh-Ritz and the updates X = S C, P = [W P] C_23 (with ||p_j||^2),
+// HX = HS C, HP = [HW HP] C_23.
+template <typename T>
+cudaError_t body_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    const int na = hasP ? 3 : 2;
+    const int m = na * k;
+    GemmBlocks<T> aS{}, aHS{}, aB{};
+    aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
+    aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
+    for (int q = 0; q < na; ++q) {
+        aB.p[q] = aHS.p[q];
+        aB.p[na + q] = aS.p[q];
+    }
+    CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));   // [S^T HS | S^T S]
+    if (hasP) {
+        k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
+        CK(cudaGetLastError());
+    }
+    CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->G + m, 2 * m, hasP ? s->pscale : nullptr, s->C, s->theta,
+                            s->status, h->stream));
+    CombineOut<T> ox{}, oh{};
+    ox.Cf = s->Cf;
+    oh.Cf = s->Cf;
+    ox.z[0] = b.X; ox.C[0] = s->C; ox.c0[0] = 0;
+    ox.z[1] = b.P; ox.C[1] = s->C + static_cast<int64_t>(k) * k; ox.c0[1] = k; ox.norm_of = 1;
+    oh.z[0] = b.HX; oh.C[0] = s->C; oh.c0[0] = 0;
+    oh.z[1] = b.HP; oh.C[1] = s->C + static_cast<int64_t>(k) * k; oh.c0[1] = k; oh.norm_of = -1;
+    CK(launch_combine<T>(n, k, na, aS, 2, ox, s->colsqP, h->num_sms, h->stream));
+    CK(launch_combine<T>(n, k, na, aHS, 2, oh, nullptr, h->num_sms, h->stream));
+    return cudaSuccess;
+}
+
+// LOBPCG_GRAPH=0 in the environment turns the graph replay off.
+bool graphs_on() {
+    static const bool on = [] {
+        const char *v = std::getenv("LOBPCG_GRAPH");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+// Capture fn's launches on the handle's stream into an executable graph.
+// Returns false (and leaves the stream out of capture) if anything fails.
+template <typename F>
+bool capture(lobpcg_ctx *h, cudaGraphExec_t *out, F fn) {
+    if (h->stream == nullptr || h->stream == cudaStreamLegacy) return false;   // no capture on the legacy stream
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();   // leave no error behind for the direct launches that follow
+        return false;
+    }
+    const cudaError_t e = fn();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    bool ok = e == cudaSuccess && e2 == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ok;
+}
+
+// One iteration after the residual.  The float32 iteration with P (every
+// iteration but the first of a run) replays two CUDA graphs captured on
+// first use -- the launches before the SpMM and those after it -- with the
+// timed SpMM launched between them; the first iteration, float64, the
+// learned form, harvesting and handles on the legacy default stream (which
+// cannot be captured) launch directly.
+template <typename T>
+cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP, int pmode, int harvest_iter = -1) {
+    const int k = s->k;
+    if constexpr (std::is_same<T, float>::value) {
+        if (hasP && harvest_iter < 0 && pmode != 3 && graphs_on() && !s->graph_failed) {
+            if (s->graph_pmode != pmode) {
+                if (s->gpre) cudaGraphExecDestroy(s->gpre);
+                if (s->gpost) cudaGraphExecDestroy(s->gpost);
+                s->gpre = s->gpost = nullptr;
+                const bool ok = capture(h, &s->gpre, [&] { return body_pre<T>(h, s, b, pmode, -1); }) &&
+                                capture(h, &s->gpost, [&] { return body_post<T>(h, s, b, true); });
+                if (!ok) {
+                    s->graph_failed = true;
+                    if (s->gpre) cudaGraphExecDestroy(s->gpre);
+                    if (s->gpost) cudaGraphExecDestroy(s->gpost);
+                    s->gpre = s->gpost = nullptr;
+                } else {
+                    s->graph_pmode = pmode;
+                }
+            }
+            if (!s->graph_failed) {
+                CK(cudaGraphLaunch(s->gpre, h->stream));
+                CK(timed_spmm<T>(h, s, b.W, b.HW, k));   // the one SpMM per iteration
+                return cudaGraphLaunch(s->gpost, h->stream);
+            }
+        }
+    }
+    CK(body_pre<T>(h, s, b, pmode, harvest_iter));
+    CK(timed_spmm<T>(h, s, b.W, b.HW, k));   // the one SpMM per iteration
+    return body_post<T>(h, s, b, hasP);
 }
 
 template <typename T>
@@ -606,6 +682,8 @@ void solver_release(lobpcg_ctx *h) {
     if (!h->solver) return;
     if (h->solver->h_buf) cudaFreeHost(h->solver->h_buf);
     if (h->solver->ev0) cudaEventDestroy(h->solver->ev0);
+    if (h->solver->gpre) cudaGraphExecDestroy(h->solver->gpre);
+    if (h->solver->gpost) cudaGraphExecDestroy(h->solver->gpost);
     if (h->solver->ev1) cudaEventDestroy(h->solver->ev1);
     delete h->solver;
     h->solver = nullptr;
