@@ -359,6 +359,8 @@ def main():
     ap.add_argument("--no-solves", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-value-only", action="store_true")
+    ap.add_argument("--fom-only", action="store_true",
+                    help="only the FOM preconditioner report (fom_apply) on the workload; for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -380,6 +382,11 @@ def main():
     A = synth.tile_matrix(p["n"], p["nnz_per_row"], seed=p["seed"], fp32=True, alloc=pinned)
     n, k, nnz = A.n, p["k"], A.nnz
     stream = torch.cuda.Stream(device=dev)
+    if args.fom_only:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "fom_apply": fom_report(pkg, A, p, stream,
+                                                                                measured_peaks()["sm_max_mhz"])}))
+        return
     h = pkg.from_csr(A, k=k, nev=p["nev"], tol=1e-6, maxiter=1000, precond="diag", stream=stream)
     X0 = synth.initial_guess(A, k, seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
     with torch.cuda.stream(stream):

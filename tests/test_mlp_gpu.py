@@ -213,8 +213,10 @@ def test_training_learns_and_solve_converges():
     A = f32_matrix(A64)
     k, nev = w["k"], w["nev"]
     X0 = synth.initial_guess(A64, k, seed=w["seed"] + synth.X0_SEED_OFFSET, fp32=True)
-    h = pkg.from_csr(A64, k=k, nev=nev, tol=1e-6, maxiter=1000, precond="mlp", polish_fp64=1, seed=77)
-    hist, used = h.precond_train(X0, harvest_iters=20, n_pairs=1 << 16, epochs=40, lr=1e-3)
+    # 5 epochs (the bench setting): longer training over-fits these pairs and
+    # has taken the learned solve from 40-56 to 194-394 iterations
+    h = pkg.from_csr(A64, k=k, nev=nev, tol=1e-6, maxiter=3000, precond="mlp", polish_fp64=1, seed=77)
+    hist, used = h.precond_train(X0, harvest_iters=20, n_pairs=1 << 16, epochs=5, lr=1e-3)
     assert used >= 20 * 313 * k * 0.9
     assert np.all(np.isfinite(hist)) and hist.min() <= hist[0], hist
     X, ev, rs, st = h.solve(X0)
