@@ -141,8 +141,22 @@ typedef struct {
 LOBPCG_API lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A,
                             const lobpcg_params *params, void *stream);
 
-/* Release every resource of the handle (NULL is accepted). */
+/* Release every resource of the handle (NULL is accepted), on the handle's
+ * device whatever device is current. */
 LOBPCG_API lobpcg_status lobpcg_destroy(lobpcg_t h);
+
+/*
+ * Device check.  Every call below that reaches the device (all but
+ * lobpcg_destroy, lobpcg_last_error and lobpcg_matrix_info) first checks
+ * that the device current on the calling thread is the one that was current
+ * at create, and returns ERR_ARG (the two ordinals in lobpcg_last_error)
+ * without touching the device otherwise.
+ *
+ * Test hook for that check: overwrite the device ordinal recorded in the
+ * handle (no CUDA call).  A handle whose ordinal is not the current device
+ * refuses every device call; set the true ordinal back to use it again.
+ */
+LOBPCG_API lobpcg_status lobpcg_test_set_device_ordinal(lobpcg_t h, int32_t device);
 
 /* One-line text of the last error on h (or of the last failed create if h is NULL). */
 LOBPCG_API const char *lobpcg_last_error(lobpcg_t h);

@@ -33,7 +33,16 @@ Readings where the paper is silent (each listed in the design notes):
     pivots span more than 1e4, i.e. cond(O) above about 1e8), P is dropped
     for that iteration;
   * on exit HX is recomputed by an explicit SpMM and convergence re-checked;
-    if it no longer holds the iteration continues from the explicit HX.
+    if it no longer holds the iteration continues from the explicit HX;
+  * ``explicit=True`` (reference runs): HX and HP are formed by explicit
+    SpMMs each iteration instead of the recurrences of eqs. upd1-upd2.  The
+    recurrences are exact in exact arithmetic, but once some columns have
+    converged to rounding level their P columns are tiny differences that
+    the unit scaling magnifies, so the recurrence HP drifts away from H P
+    and the Ritz values can fall below the eigenvalues (k = 20, n = 8000:
+    the residual climbed from 1e-13 back to 5e-4 and stayed there).
+    Explicit products cost two extra SpMMs per iteration and reach the
+    dense eigenvalues to 3e-14.
 """
 from __future__ import annotations
 
@@ -134,6 +143,18 @@ def resid_norms(R, X, theta, normG, mode=0):
     return rn / (normG * xn)
 
 
+def dense_lowest(A, nev: int):
+    """The nev smallest eigenvalues of H and their eigenvectors, from the
+    dense matrix: the plain definition of what LOBPCG computes (Section 2,
+    eq. tracemin), by a library symmetric eigensolver (LAPACK through
+    ``scipy.linalg.eigh``).  For small n only (n^2 doubles).  Pinned against
+    the 1-D Laplacian closed form and the Jacobi oracle (tests)."""
+    import scipy.linalg
+    from . import to_dense
+    w, V = scipy.linalg.eigh(to_dense(A), subset_by_index=[0, nev - 1])
+    return w, V
+
+
 @dataclass
 class Result:
     evals: np.ndarray
@@ -150,12 +171,14 @@ class Result:
 def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
            precond: str = "diag", resid_mode: int = 0, tile: int = 64,
            precond_fn=None, max_explicit_restarts: int = 5, fom_steps: int = 4,
-           fom_tile_ptr=None) -> Result:
+           fom_tile_ptr=None, explicit: bool = False) -> Result:
     """FP64 block LOBPCG on the symmetric H stored as its lower triangle ``A``.
 
     ``precond``: "none", "diag", "bjacobi" (64-row tiles), "fom" (``fom_steps``
     FOM iterations per diagonal tile: ``fom_tile_ptr``, else 64-row tiles) or "custom"
-    (``precond_fn(R, theta) -> W``).  Returns the nev leftmost Ritz pairs."""
+    (``precond_fn(R, theta) -> W``).  ``explicit``: HX and HP by explicit
+    SpMMs instead of the recurrences (see the module notes).  Returns the nev
+    leftmost Ritz pairs."""
     X0 = np.asarray(X0, dtype=np.float64)
     n, k = X0.shape
     assert 1 <= nev <= k
@@ -212,6 +235,8 @@ def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
             pn = np.linalg.norm(P, axis=0)
             pn[pn == 0.0] = 1.0
             P, HP = P / pn, HP / pn
+            if explicit:
+                HP = spmm_tri(A, P)
         kw = W.shape[1]
         try:
             if P is None:
@@ -226,7 +251,7 @@ def lobpcg(A, X0: np.ndarray, nev: int, tol: float = 1e-6, maxiter: int = 1000,
             HS = np.hstack([HX, HW])
             theta_new, C = rayleigh_ritz(S.T @ HS, S.T @ S, k)
         X = S @ C                                     # eq. (xupd)
-        HX = HS @ C                                   # eq. (upd1)
+        HX = spmm_tri(A, X) if explicit else HS @ C   # eq. (upd1)
         P = S[:, k:] @ C[k:]                          # eq. (pupd)
         HP = HS[:, k:] @ C[k:]                        # eq. (upd2)
         theta = theta_new

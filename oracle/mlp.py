@@ -93,8 +93,10 @@ def apply(p: dict, R: np.ndarray, d: np.ndarray, theta: np.ndarray, normG: float
     w_T = 0).  A non-finite c_T is dropped; a c_T longer than D_theta^{-1} r_T
     is scaled down to its length.
     Pinned through its pieces: the forward pass by the gradient checks, the
-    diagonal part by apply_diag's own pins, and a zero output layer giving
-    exactly the diagonal solve."""
+    diagonal part by apply_diag's own pins, a zero output layer giving
+    exactly the diagonal solve, and hand-worked tiles with a constant output
+    layer (W2 = 0, b2 = c) that fix the scale s / g and the length bound,
+    kept and clamped, on a full and a ragged tile."""
     n, k = R.shape
     W = apply_diag(d, R, theta)
     for t0 in range(0, n, TILE):

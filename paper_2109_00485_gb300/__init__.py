@@ -96,6 +96,8 @@ def load():
     L.lobpcg_rayleigh_ritz.restype = st
     L.lobpcg_rayleigh_ritz_noalloc.argtypes = [vp, vp, vp, i32, i32, vp, vp]
     L.lobpcg_rayleigh_ritz_noalloc.restype = st
+    L.lobpcg_test_set_device_ordinal.argtypes = [vp, i32]
+    L.lobpcg_test_set_device_ordinal.restype = st
     L.lobpcg_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(_Stats)]
     L.lobpcg_solve.restype = st
     L.lobpcg_davidson.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(_Stats)]
@@ -348,6 +350,10 @@ class Handle:
         if self._h:
             load().lobpcg_destroy(self._h)
             self._h = ctypes.c_void_p(0)
+
+    def lobpcg_test_set_device_ordinal(self, device: int):
+        """Test hook: overwrite the device ordinal recorded in the handle."""
+        _check(self._h, load().lobpcg_test_set_device_ordinal(self._h, int(device)))
 
     # -- conveniences with the same meaning ---------------------------------
     spmm_sym = lobpcg_spmm_sym

@@ -166,9 +166,23 @@ lobpcg_status lobpcg_create(lobpcg_t *out, const lobpcg_matrix *A, const lobpcg_
 
 lobpcg_status lobpcg_destroy(lobpcg_t h) {
     if (!h) return LOBPCG_OK;
+    // free on the handle's device whatever device the caller has current
+    int cur = -1;
+    bool switched = false;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) {
+        switched = cudaSetDevice(h->device) == cudaSuccess;
+        if (!switched) cudaGetLastError();
+    }
     if (h->stream) cudaStreamSynchronize(h->stream);
     release(h);
     delete h;
+    if (switched) cudaSetDevice(cur);
+    return LOBPCG_OK;
+}
+
+lobpcg_status lobpcg_test_set_device_ordinal(lobpcg_t h, int32_t device) {
+    if (!h) return LOBPCG_ERR_ARG;
+    h->device = device;
     return LOBPCG_OK;
 }
 
@@ -196,6 +210,7 @@ lobpcg_status lobpcg_matrix_info(lobpcg_t h, lobpcg_info *info) {
 
 lobpcg_status lobpcg_sync(lobpcg_t h) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sync");
@@ -208,6 +223,7 @@ lobpcg_status lobpcg_sync(lobpcg_t h) {
 
 lobpcg_status lobpcg_spmm_sym(lobpcg_t h, const float *X, float *Y, int32_t k) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!X || !Y) return fail(h, LOBPCG_ERR_ARG, "X or Y is NULL");
     if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     const size_t bytes = sizeof(float) * static_cast<size_t>(h->T.n) * k;
@@ -240,6 +256,7 @@ lobpcg_status lobpcg_spmm_sym(lobpcg_t h, const float *X, float *Y, int32_t k) {
 
 lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double *Y, int32_t k) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!X || !Y) return fail(h, LOBPCG_ERR_ARG, "X or Y is NULL");
     if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     const size_t bytes = sizeof(double) * static_cast<size_t>(h->T.n) * k;
@@ -252,6 +269,7 @@ lobpcg_status lobpcg_spmm_sym_f64(lobpcg_t h, const double *X, double *Y, int32_
 lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *theta, float *W, int32_t k,
                                    int32_t mode) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!R || !W || !theta) return fail(h, LOBPCG_ERR_ARG, "R, W or theta is NULL");
     if (k < 1 || k > 32) return fail(h, LOBPCG_ERR_ARG, "k must be in [1, 32]");
     if (mode < 0 || mode > 4) return fail(h, LOBPCG_ERR_ARG, "mode must be 0..4");
@@ -270,6 +288,7 @@ lobpcg_status lobpcg_precond_apply(lobpcg_t h, const float *R, const double *the
 lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, int32_t m, int32_t k, double *C,
                                    double *theta) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!S || !HS || !C || !theta) return fail(h, LOBPCG_ERR_ARG, "S, HS, C or theta is NULL");
     if (m < 1 || m > 96 || k < 1 || k > m) return fail(h, LOBPCG_ERR_ARG, "need 1 <= k <= m <= 96");
     double *G = nullptr, *O = nullptr;
@@ -295,6 +314,7 @@ lobpcg_status lobpcg_rayleigh_ritz(lobpcg_t h, const float *S, const float *HS, 
 
 lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, lobpcg_stats *st) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!X) return fail(h, LOBPCG_ERR_ARG, "X is NULL");
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
     if (h->params.precond == 3 && !h->mlp.ready)
@@ -308,6 +328,7 @@ lobpcg_status lobpcg_solve(lobpcg_t h, float *X, double *evals, double *resid, l
 lobpcg_status lobpcg_davidson(lobpcg_t h, float *X, int32_t max_blocks, double *evals, double *resid,
                               lobpcg_stats *st) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!X) return fail(h, LOBPCG_ERR_ARG, "X is NULL");
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
     if (max_blocks < 2 || max_blocks > 6 || max_blocks * h->params.k > 96)
@@ -322,6 +343,7 @@ lobpcg_status lobpcg_davidson(lobpcg_t h, float *X, int32_t max_blocks, double *
 
 lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double *theta, lobpcg_stats *st) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (steps < 0) return fail(h, LOBPCG_ERR_ARG, "steps must be >= 0");
     if (!h->solver) return fail(h, LOBPCG_ERR_UNSUPPORTED, "solver workspace missing");
     if (h->params.precond == 3 && !h->mlp.ready)
@@ -334,6 +356,7 @@ lobpcg_status lobpcg_iterate(lobpcg_t h, const float *X0, int32_t steps, double 
 
 lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X) {
     if (!h || !X) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     cudaError_t e = copy_x_f64(h, X);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_x_f64");
     return LOBPCG_OK;
@@ -341,6 +364,7 @@ lobpcg_status lobpcg_get_x_f64(lobpcg_t h, double *X) {
 
 lobpcg_status lobpcg_mlp_set_params(lobpcg_t h, const float *params, int64_t count) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!params || count != MLP_NPARAM_CALLER) return fail(h, LOBPCG_ERR_ARG, "params NULL or count != 49728");
     cudaError_t e = mlp_set_params(h, params, is_host_ptr(params));
@@ -350,6 +374,7 @@ lobpcg_status lobpcg_mlp_set_params(lobpcg_t h, const float *params, int64_t cou
 
 lobpcg_status lobpcg_mlp_get_params(lobpcg_t h, float *out, int64_t count, int32_t which) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!out || count != MLP_NPARAM_CALLER) return fail(h, LOBPCG_ERR_ARG, "out NULL or count != 49728");
     if (which != 0 && which != 1) return fail(h, LOBPCG_ERR_ARG, "which must be 0 (weights) or 1 (gradients)");
@@ -360,6 +385,7 @@ lobpcg_status lobpcg_mlp_get_params(lobpcg_t h, float *out, int64_t count, int32
 
 lobpcg_status lobpcg_mlp_forward(lobpcg_t h, const float *Xin, int64_t B, float *Y) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!Xin || !Y || B < 1 || B > (int64_t(1) << 30)) return fail(h, LOBPCG_ERR_ARG, "Xin/Y NULL or B out of range");
     cudaError_t e = mlp_forward_rows(h, Xin, B, Y);
@@ -369,6 +395,7 @@ lobpcg_status lobpcg_mlp_forward(lobpcg_t h, const float *Xin, int64_t B, float 
 
 lobpcg_status lobpcg_mlp_grad(lobpcg_t h, const float *Xin, const float *T, int64_t B, double *loss) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!Xin || !T || B < 1 || B > (int64_t(1) << 30)) return fail(h, LOBPCG_ERR_ARG, "Xin/T NULL or B out of range");
     double l = 0.0;
@@ -380,6 +407,7 @@ lobpcg_status lobpcg_mlp_grad(lobpcg_t h, const float *Xin, const float *T, int6
 
 lobpcg_status lobpcg_mlp_adam(lobpcg_t h, float lr) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!(lr > 0.f)) return fail(h, LOBPCG_ERR_ARG, "lr must be > 0");
     cudaError_t e = mlp_adam(h, lr);
@@ -390,6 +418,7 @@ lobpcg_status lobpcg_mlp_adam(lobpcg_t h, float lr) {
 lobpcg_status lobpcg_precond_train(lobpcg_t h, int32_t harvest_iters, int64_t n_pairs, int32_t epochs,
                                    const float *X0, float lr, double *loss_hist, int64_t *pairs_used) {
     if (!h) return LOBPCG_ERR_ARG;
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!h->mlp.P) return fail(h, LOBPCG_ERR_UNSUPPORTED, "learned form needs params.precond = 3 at create");
     if (!X0) return fail(h, LOBPCG_ERR_ARG, "X0 is NULL");
     if (harvest_iters < 1 || epochs < 0 || n_pairs < MLP_BATCH || n_pairs > (int64_t(1) << 32) || !(lr > 0.f))

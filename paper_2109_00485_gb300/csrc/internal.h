@@ -111,6 +111,26 @@ struct lobpcg_ctx {
 
 namespace lobpcg {
 
+// Every buffer, stream and graph of a handle belongs to the device that was
+// current at create, so every call that touches the device must run with
+// that device current.  Returns false (with the reason in last_error) when
+// another device is current or the current device cannot be read.
+inline bool device_ok(lobpcg_ctx *h) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->last_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return false;
+    }
+    if (cur != h->device) {
+        h->last_error = "the handle was created on device " + std::to_string(h->device) + " but device " +
+                        std::to_string(cur) + " is current; make the handle's device current first";
+        return false;
+    }
+    return true;
+}
+
 // tiling.cu
 cudaError_t build_tiled(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t *col, const void *val,
                         bool val_fp64, std::string &err, lobpcg_status &st);

@@ -53,6 +53,9 @@ using namespace lobpcg;
 extern "C" lobpcg_status lobpcg_rayleigh_ritz_noalloc(lobpcg_t h, const float *S, const float *HS, int32_t m,
                                                       int32_t k, double *C, double *theta) {
     if (!h) return LOBPCG_ERR_ARG;
+    // the address lookup below resolves the array on the current device and
+    // caches it under h->device: both must be the same device
+    if (!device_ok(h)) return LOBPCG_ERR_ARG;
     if (!S || !HS || !C || !theta) {
         h->last_error = "S, HS, C or theta is NULL";
         return LOBPCG_ERR_ARG;

@@ -133,9 +133,18 @@ def test_tile_apply_matches_oracle():
     theta = np.linspace(-2.0, 30.0, k)
     W = h.precond_apply(torch.from_numpy(R).cuda(), torch.from_numpy(theta).cuda(), mode="mlp").cpu().numpy()
     normG = h.info()["gershgorin"]
-    Wo = omlp.apply(rounded(p), R.astype(np.float64), oracle.diagonal(A), theta, normG)
+    d = oracle.diagonal(A)
+    Wo = omlp.apply(rounded(p), R.astype(np.float64), d, theta, normG)
+    Wd = apply_diag(d, R.astype(np.float64), theta)
     for j in range(k):
         assert rel(W[:, j], Wo[:, j]) <= 1e-2, j
+    # element by element: each row within 2 % of the largest correction of
+    # its tile column (bfloat16 operands: 2^-9 per rounding, two layers)
+    for t0 in range(0, A.n, 64):
+        sl = slice(t0, min(t0 + 64, A.n))
+        cmax = np.abs(Wo[sl] - Wd[sl]).max(axis=0)
+        err = np.abs(W[sl] - Wo[sl])
+        assert np.all(err <= 1e-5 * np.abs(Wo[sl]) + 2e-2 * cmax[None, :]), (t0, (err / (cmax + 1e-300)).max())
     assert not W[64:128, 2].any()
     h.destroy()
 

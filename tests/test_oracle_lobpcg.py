@@ -52,6 +52,37 @@ def test_lobpcg_laplacian_closed_form():
     assert np.max(np.abs(r.evals - exact) / exact) < 1e-9
 
 
+def test_dense_lowest_closed_form_and_jacobi():
+    """The dense reference (the plain definition: nev smallest eigenvalues of
+    H) against the 1-D Laplacian closed form and the Jacobi oracle."""
+    n = 60
+    w, V = olb.dense_lowest(laplacian_csr(n), 5)
+    exact = np.array([2 - 2 * math.cos(j * math.pi / (n + 1)) for j in range(1, 6)])
+    assert np.max(np.abs(w - exact)) < 1e-13
+    A = synth.tile_matrix(150, 40, seed=21)
+    w, V = olb.dense_lowest(A, 7)
+    wj, _ = oracle.jacobi_eig(oracle.to_dense(A))
+    assert np.max(np.abs(w - wj[:7])) < 1e-12 * np.abs(wj).max()
+    H = oracle.to_dense(A)
+    assert np.max(np.abs(H @ V - V * w)) < 1e-11 * np.abs(wj).max()
+
+
+@pytest.mark.parametrize("k,nev,pc", [(12, 6, "diag"), (20, 10, "diag"), (16, 8, "bjacobi")])
+def test_lobpcg_explicit_products_vs_dense(k, nev, pc):
+    """The explicit-product form (HX, HP by SpMM each iteration) reaches the
+    dense eigenvalues at tol 1e-10 for block sizes up to 20."""
+    A = synth.tile_matrix(1500, 50, seed=23)
+    lam, _ = olb.dense_lowest(A, nev)
+    X0 = synth.initial_guess(A, k, seed=1023)
+    r = olb.lobpcg(A, X0, nev, tol=1e-10, maxiter=500, precond=pc, explicit=True)
+    assert r.converged
+    assert np.max(np.abs(r.evals - lam) / np.maximum(np.abs(lam), 1e-3)) < 1e-10
+    H = oracle.to_dense(A)
+    R = H @ r.X - r.X * r.evals
+    rho = np.linalg.norm(R, axis=0) / (np.abs(r.evals) * np.linalg.norm(r.X, axis=0))
+    assert np.all(rho <= 1e-10 * 1.01)
+
+
 def test_ritz_values_monotone():
     """span(S_i) contains span(X_i), so each Ritz value can only decrease
     (Courant-Fischer), up to rounding."""

@@ -103,3 +103,58 @@ def test_untrained_apply_is_the_diagonal_solve():
     W2 = mlp.apply(small_params(2), R, d, theta, 12.0)
     for t0 in (0, 64, 128):
         assert not np.allclose(W2[t0:t0 + 64], W[t0:t0 + 64])
+
+
+def _constant_output_params(c: np.ndarray) -> dict:
+    """W2 = 0 and b2 = c: the network returns c whatever its input."""
+    p = mlp.init_params(synth.normals(mlp.N_HID * mlp.N_IN, 3, 1))
+    p["b1"] = np.ones(mlp.N_HID)
+    p["b2"] = c.copy()
+    return p
+
+
+def test_apply_scale_and_length_bound_by_hand():
+    """w_T = r_T / (d - theta) + (s / g) y with y = b2 (W2 = 0), worked by
+    hand on one 64-row tile: r = 1 on rows 0..15 and 0 elsewhere, so
+    s = ||r|| = 4; d = 3; g = ||H||_G = 8.
+      column 0, theta = 1, b2 = 0.25: diagonal part 0.5 on rows 0..15,
+        ||D^-1 r|| = 2; correction (4/8) 0.25 = 0.125 on every row, length
+        0.125 * 8 = 1 <= 2, kept: w = 0.625 (rows 0..15), 0.125 (others).
+      column 1, theta = 1, b2 = 1: correction 0.5 on every row, length 4 > 2,
+        scaled by 2/4: w = 0.75 (rows 0..15), 0.25 (others).
+      column 2, theta = 2, b2 = 1: diagonal part 1 on rows 0..15, length 4;
+        correction length 4, not longer, kept: w = 1.5, 0.5.
+    A slip in the scale (g/s, s^2/g) or in the bound (direction, dn/cn
+    inverted) changes at least one of these values."""
+    r = np.zeros(64)
+    r[:16] = 1.0
+    d = np.full(64, 3.0)
+    g = 8.0
+    cases = [(1.0, 0.25, 0.625, 0.125), (1.0, 1.0, 0.75, 0.25), (2.0, 1.0, 1.5, 0.5)]
+    for theta, b2, top, rest in cases:
+        p = _constant_output_params(np.full(64, b2))
+        W = mlp.apply(p, r[:, None], d, np.array([theta]), g)[:, 0]
+        want = np.where(np.arange(64) < 16, top, rest)
+        assert np.array_equal(W, want), (theta, b2, W[:3], W[-3:])
+
+
+def test_apply_bound_keeps_direction_and_ragged_tile():
+    """The length bound scales the correction, it does not turn it: with a
+    non-constant b2 the clamped correction is b2 times one positive factor
+    fixed by hand.  A ragged last tile (n = 64 + 10) uses its own 10 rows of
+    r, d and of the network's output only.  Tile 2 (rows 64..73): r = 2 on
+    all 10 rows, s = 2 sqrt(10), d = 5, theta = 1: D^-1 r = 0.5 per row,
+    length 0.5 sqrt(10); b2[i] = 1 + i (i = 0..9 used): correction
+    (s/g) b2 = (2 sqrt(10)/8)(1 + i), its length (sqrt(10)/4) sqrt(385) is
+    longer, so it is scaled to 0.5 sqrt(10): w_i = 0.5 + 0.5 sqrt(10)(1 + i)/sqrt(385)."""
+    n = 74
+    R = np.zeros((n, 1))
+    R[64:, 0] = 2.0
+    d = np.full(n, 5.0)
+    c = np.arange(64, dtype=np.float64) + 1.0
+    p = _constant_output_params(c)
+    W = mlp.apply(p, R, d, np.array([1.0]), 8.0)[:, 0]
+    assert not W[:64].any()                          # s = 0 tile: w = 0
+    i = np.arange(10)
+    want = 0.5 + 0.5 * np.sqrt(10.0) * (1.0 + i) / np.sqrt(385.0)
+    assert np.allclose(W[64:], want, rtol=1e-14, atol=0), (W[64:], want)
