@@ -59,6 +59,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// try_wait that may suspend the thread for up to `ns` nanoseconds while the
+// phase is incomplete (instead of returning at once), so that many waiting
+// warps do not fill the issue slots with polls.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait by suspending polls: at most WAIT_LIMIT_SLEEP polls of up to
+// 20 us each (a few tens of seconds if every poll slept its limit, much less
+// if the hint is not honoured).
+constexpr uint32_t WAIT_LIMIT_SLEEP = 1u << 20;
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < WAIT_LIMIT_SLEEP; ++it)
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    return false;
+}
+
 // L2 policy: streamed data that is read once.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;

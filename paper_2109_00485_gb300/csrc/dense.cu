@@ -1492,6 +1492,17 @@ static bool gram_umma_enabled() {
     return on != 0;
 }
 
+// LOBPCG_GRAM=tc keeps float32 Grams on the mma.sync kernel k_gram_tc
+// (for comparison); by default they go to the CUDA-core pair kernel
+// (gram_ff.cu) when it takes the shape.
+static bool gram_tc_forced() {
+    static const int on = [] {
+        const char *v = getenv("LOBPCG_GRAM");
+        return (v && strcmp(v, "tc") == 0) ? 1 : 0;
+    }();
+    return on != 0;
+}
+
 template <typename T>
 cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmBlocks<T> b, double *M, int num_sms,
                         cudaStream_t s, int *err) {
@@ -1499,6 +1510,24 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
     if constexpr (std::is_same<T, float>::value) {
         if (err && gram_umma_enabled() && gram_umma_ok(k, na, a.p, nb, b.p))
             return launch_gram_umma(n, k, na, a.p, nb, b.p, M, err, num_sms, s);
+        if (err && !gram_tc_forced() && na * nb <= 16) {
+            // every (A block, B block) pair on the CUDA-core kernel
+            const float *blk[12];
+            int nblk = 0;
+            auto uq = [&](const float *p) {
+                for (int q = 0; q < nblk; ++q)
+                    if (blk[q] == p) return q;
+                blk[nblk] = p;
+                return nblk++;
+            };
+            GramPair pairs[16];
+            int np = 0;
+            for (int qa = 0; qa < na; ++qa)
+                for (int qb = 0; qb < nb; ++qb) pairs[np++] = GramPair{uq(a.p[qa]), uq(b.p[qb]), qa, qb, 0, 0, 0};
+            const int units = np * (k / 4) * (k / 4);
+            if (nblk <= 8 && gram_pairs_fit(k, nblk, blk, np, units))
+                return launch_gram_pairs(n, k, nblk, blk, np, pairs, M, mb, ma, true, err, num_sms, s);
+        }
     }
     cudaError_t e = cudaMemsetAsync(M, 0, sizeof(double) * ma * mb, s);
     if (e != cudaSuccess) return e;

@@ -44,6 +44,26 @@ cudaError_t launch_gram(int64_t n, int k, int na, GemmBlocks<T> a, int nb, GemmB
 bool gram_umma_ok(int k, int na, const float *const *ap, int nb, const float *const *bp);
 cudaError_t launch_gram_umma(int64_t n, int k, int na, const float *const *ap, int nb, const float *const *bp,
                              double *M, int *err, int num_sms, cudaStream_t s);
+// One k x k output block of a Gram pair list (gram_ff.cu): M block at block
+// row ro, block column co (units of k) = blk[a]^T blk[b].  GRAM_SYM: a
+// symmetric block (only its lower half is computed, the upper half written
+// as its transpose inside the same block); GRAM_MIRROR: the block is also
+// written transposed at block (mro, mco).
+constexpr int GRAM_SYM = 1;
+constexpr int GRAM_MIRROR = 2;
+struct GramPair {
+    int a, b, ro, co, flags, mro, mco;
+};
+bool gram_pairs_ok(int k, int nblk, const float *const *blk, int npairs);
+// gram_pairs_ok and the pairs' sub-tile units (k/4 squared per pair, fewer
+// for GRAM_SYM) within what one CTA of the kernel holds.
+bool gram_pairs_fit(int k, int nblk, const float *const *blk, int npairs, int units);
+// M (ldm_rows x ldm, FP64, row-major; zeroed first when `zero`) += the
+// listed blocks.  float32 blocks n x k, 16-byte aligned, k % 4 == 0,
+// k <= 32, at most 8 distinct blocks and 16 pairs.  err: device error word
+// for the bounded waits.
+cudaError_t launch_gram_pairs(int64_t n, int k, int nblk, const float *const *blk, int npairs, const GramPair *pairs,
+                              double *M, int ldm, int ldm_rows, bool zero, int *err, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
                            int num_sms, cudaStream_t s);

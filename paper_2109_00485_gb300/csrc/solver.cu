@@ -283,6 +283,68 @@ cudaError_t body_pre(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, int pmode, int
     return cudaSuccess;
 }
 
+// LOBPCG_GRAM_POST=full computes every block of the post-SpMM Gram
+// (for comparison with the lower-block form).
+bool gram_post_forced_full() {
+    static const bool on = [] {
+        const char *v = std::getenv("LOBPCG_GRAM_POST");
+        return v && std::strcmp(v, "full") == 0;
+    }();
+    return on;
+}
+
+// [S^T HS | S^T S] (m x 2m, FP64, m = na k) for S = [X W P] (na = 3) or
+// [X W] (na = 2), HS = [HX HW HP].  float32 blocks go to the CUDA-core pair
+// kernel with the diagonal and lower blocks only: the Rayleigh-Ritz step
+// averages G[i][j] and G[j][i], so each upper block is written as the
+// transpose of its lower partner.  Of the two products of an off-diagonal G block the
+// one with HW, this iteration's explicit SpMM, is taken (X^T HW, P^T HW);
+// the (X, P) block is P^T HX.  Other shapes: all blocks by launch_gram.
+template <typename T>
+cudaError_t gram_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, int na) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    const int m = na * k;
+    if constexpr (std::is_same<T, float>::value) {
+        const float *blk[6] = {b.X, b.W, b.P, b.HX, b.HW, b.HP};
+        if (na == 2) {
+            blk[2] = b.HX;
+            blk[3] = b.HW;
+        }
+        const int X = 0, W = 1, P = 2, HX = na, HW = na + 1;
+        GramPair pr[12];
+        int np = 0;
+        // diagonal blocks in full: a warp then holds exactly one pair (k = 16)
+        // and reads one 128-byte line per load (packed lower halves put two
+        // pairs in many warps and doubled the shared-memory wavefronts)
+        for (int i = 0; i < na; ++i) {
+            pr[np++] = GramPair{i, na + i, i, i, 0, 0, 0};                    // S_i^T HS_i
+            pr[np++] = GramPair{i, i, i, na + i, 0, 0, 0};                    // S_i^T S_i
+        }
+        pr[np++] = GramPair{X, HW, 0, 1, GRAM_MIRROR, 1, 0};                 // X^T HW
+        pr[np++] = GramPair{W, X, 1, na + 0, GRAM_MIRROR, 0, na + 1};        // W^T X
+        if (na == 3) {
+            pr[np++] = GramPair{P, HW, 2, 1, GRAM_MIRROR, 1, 2};             // P^T HW
+            pr[np++] = GramPair{P, HX, 2, 0, GRAM_MIRROR, 0, 2};             // P^T HX
+            pr[np++] = GramPair{P, X, 2, na + 0, GRAM_MIRROR, 0, na + 2};    // P^T X
+            pr[np++] = GramPair{P, W, 2, na + 1, GRAM_MIRROR, 1, na + 2};    // P^T W
+        }
+        const int T4 = k / 4;
+        const int units = np * T4 * T4;
+        if (!gram_post_forced_full() && gram_pairs_fit(k, 2 * na, blk, np, units))
+            return launch_gram_pairs(n, k, 2 * na, blk, np, pr, s->G, 2 * m, m, true, h->d_err, h->num_sms,
+                                     h->stream);
+    }
+    GemmBlocks<T> aS{}, aB{};
+    aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
+    const T *hs[3] = {b.HX, b.HW, b.HP};
+    for (int q = 0; q < na; ++q) {
+        aB.p[q] = hs[q];
+        aB.p[na + q] = aS.p[q];
+    }
+    return launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err);
+}
+
 // After the SpMM: Gram matrices of S = [X W P], HS = [HX HW HP],
 // Rayleigh-Ritz and the updates X = S C, P = [W P] C_23 (with ||p_j||^2),
 // HX = HS C, HP = [HW HP] C_23.
@@ -292,14 +354,10 @@ cudaError_t body_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
     const int64_t n = h->T.n;
     const int na = hasP ? 3 : 2;
     const int m = na * k;
-    GemmBlocks<T> aS{}, aHS{}, aB{};
+    GemmBlocks<T> aS{}, aHS{};
     aS.p[0] = b.X; aS.p[1] = b.W; aS.p[2] = b.P;
     aHS.p[0] = b.HX; aHS.p[1] = b.HW; aHS.p[2] = b.HP;
-    for (int q = 0; q < na; ++q) {
-        aB.p[q] = aHS.p[q];
-        aB.p[na + q] = aS.p[q];
-    }
-    CK(launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));   // [S^T HS | S^T S]
+    CK(gram_post<T>(h, s, b, na));   // [S^T HS | S^T S]
     if (hasP) {
         k_pscale<<<1, 64, 0, h->stream>>>(k, s->colsqP, s->pscale);
         CK(cudaGetLastError());
