@@ -45,6 +45,7 @@ struct SolverState {
     Blocks<double> d;
     double *G = nullptr, *O = nullptr, *C = nullptr, *theta = nullptr, *norms = nullptr, *colsqP = nullptr;
     double *pscale = nullptr, *B = nullptr, *Tm = nullptr, *Cproj = nullptr;
+    double *B2 = nullptr;        // 2k x k: [X^T W ; W^T W] (second orthonormalisation pass)
     double *Gx = nullptr;        // k x 2k: [X^T HX | X^T X] in float64 (mixed refinement)
     double *Rt = nullptr;        // k x 2k: R^T [W P] (mixed refinement)
     float *Cf = nullptr;         // float copies of combine coefficients
@@ -84,6 +85,32 @@ __global__ void k_proj_coef(int k, const double *B, double *Cp) {
     for (int e = threadIdx.x; e < 2 * k * k; e += blockDim.x) {
         const int r = e / k, j = e % k;
         Cp[e] = (r < k) ? (r == j ? 1.0 : 0.0) : -B[(r - k) * k + j];
+    }
+}
+
+// Omega = W^T W - S^T S with S = X^T W: B2 = [S ; W^T W] (2k x k).  The
+// Gram of W - X S when X has orthonormal columns (the Pythagorean form of
+// block Gram-Schmidt: Carson, Lund, Rozloznik, Thomas 2022).
+__global__ void k_pip_omega(int k, const double *B2, double *Om) {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e % k;
+        double v = B2[(k + i) * k + j];
+        for (int l = 0; l < k; ++l) v -= B2[l * k + i] * B2[l * k + j];
+        Om[e] = v;
+    }
+}
+
+// C = [T ; -S T] (2k x k): (W - X S) T = [W X] C.
+__global__ void k_pip_coef(int k, const double *B2, const double *Tm, double *C) {
+    for (int e = threadIdx.x; e < 2 * k * k; e += blockDim.x) {
+        const int r = e / k, j = e % k;
+        if (r < k) {
+            C[e] = Tm[r * k + j];
+        } else {
+            double v = 0.0;
+            for (int l = 0; l < k; ++l) v -= B2[(r - k) * k + l] * Tm[l * k + j];
+            C[e] = v;
+        }
     }
 }
 
@@ -227,6 +254,38 @@ cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     return launch_combine<T>(n, k, 1, aw, 1, o2, nullptr, h->num_sms, h->stream);  // W <- W T
 }
 
+// The second orthonormalisation pass in one read of X and W and one combine
+// (float32 blocks the Gram pair kernel takes): [X^T W ; W^T W] by one Gram
+// launch, Omega = W^T W - S^T S (S = X^T W) is the Gram of W - X S, its
+// Cholesky-QR (or SVQB) factor T, and W <- (W - X S) T = [W X] [T ; -S T].
+// After the first pass W is orthogonal to X to working precision, so the
+// subtraction in Omega loses nothing (the first pass, where W may lie
+// nearly in span(X), forms W - X S explicitly).  Other cases: orth_pass.
+template <typename T>
+cudaError_t orth_pass_pip(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
+    const int k = s->k;
+    const int64_t n = h->T.n;
+    if constexpr (std::is_same<T, float>::value) {
+        const float *blk[2] = {b.X, b.W};
+        const GramPair pr[2] = {GramPair{0, 1, 0, 0, 0, 0, 0}, GramPair{1, 1, 1, 0, 0, 0, 0}};
+        if (gram_pairs_fit(k, 2, blk, 2, 2 * (k / 4) * (k / 4))) {
+            CK(launch_gram_pairs(n, k, 2, blk, 2, pr, s->B2, k, 2 * k, true, h->d_err, h->num_sms, h->stream));
+            k_pip_omega<<<1, 256, 0, h->stream>>>(k, s->B2, s->B);
+            CK(cudaGetLastError());
+            CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
+            k_pip_coef<<<1, 256, 0, h->stream>>>(k, s->B2, s->Tm, s->Cproj);
+            CK(cudaGetLastError());
+            GemmBlocks<T> awx{};
+            awx.p[0] = b.W;
+            awx.p[1] = b.X;
+            CombineOut<T> o{};
+            o.z[0] = b.W; o.C[0] = s->Cproj; o.c0[0] = 0; o.norm_of = -1; o.Cf = s->Cf;
+            return launch_combine<T>(n, k, 2, awx, 1, o, nullptr, h->num_sms, h->stream);
+        }
+    }
+    return orth_pass<T>(h, s, b);
+}
+
 // Rayleigh-Ritz on X alone (Algorithm 1, lines 1-2): X <- X C, HX <- HX C.
 template <typename T>
 cudaError_t rr_on_x(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
@@ -279,7 +338,7 @@ cudaError_t body_pre(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, int pmode, int
     if (pmode == 3 || pmode == 4) CK(precond_apply<T>(h, pmode, k, b.W, s->theta, b.W, h->stream));
     // orthonormalise W against X and itself
     CK(orth_pass<T>(h, s, b));
-    CK(orth_pass<T>(h, s, b));
+    CK(orth_pass_pip<T>(h, s, b));
     return cudaSuccess;
 }
 
@@ -642,7 +701,7 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         // preconditioner (the diagonal one was applied in the residual)
         if (pmode >= 2) CK(precond_apply<float>(h, pmode, k, f.W, s->theta, f.W, h->stream));
         CK(orth_pass<float>(h, s, f));
-        CK(orth_pass<float>(h, s, f));
+        CK(orth_pass_pip<float>(h, s, f));
         CK(timed_spmm<float>(h, s, f.W, f.HW, k));
         const int na = hasP ? 3 : 2;
         const int m = na * k;
@@ -723,6 +782,7 @@ cudaError_t solver_setup(lobpcg_ctx *h) {
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->B), sizeof(double) * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Tm), sizeof(double) * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Cproj), sizeof(double) * 2 * k * k));
+    CK(dev_alloc(h, reinterpret_cast<void **>(&s->B2), sizeof(double) * 2 * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Gx), sizeof(double) * 2 * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->Rt), sizeof(double) * 2 * k * k));
     CK(dev_alloc(h, reinterpret_cast<void **>(&s->status), sizeof(int) * 4));
