@@ -129,10 +129,11 @@ class ClockSampler:
 
 
 # Kernel launches of one LOBPCG iteration with a P block (from the ncu launch
-# list of this bench: resid, 2 x (4 Gram-type, projection, Cholesky-QR
-# factor, 2 combine, 2 coefficient casts), SpMM, Gram, P scaling,
-# Rayleigh-Ritz, 2 x (cast, combine) = 25).
-LAUNCHES_PER_ITERATION = 25
+# list of this bench): residual; first orthonormalisation pass (2 Gram,
+# projection coefficients, Cholesky-QR factor, 2 casts, 2 combines); second
+# pass (Gram, Omega, factor, coefficients, cast, combine); SpMM; Gram,
+# P scaling, Rayleigh-Ritz, 2 x (cast, combine) = 23.
+LAUNCHES_PER_ITERATION = 23
 
 
 def aggregate(total_ms: float, bytes_per_step: int, steps: int, world: int, device=None):
@@ -338,6 +339,83 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
     return out
 
 
+def largest_report(pkg, stream, peak_gbs: float, workload: str = "largest_n8m") -> dict:
+    """The largest workload (n = 8,000,000, ~250 stored entries per row, about
+    2.0 G stored entries, k = 20, nev = 10): the SpMM kernel's time and
+    fraction of the measured HBM peak, one LOBPCG iteration, and the
+    time-to-1e-6 of the diagonal form and of the learned form (trained as in
+    lobpcg_solves; a tile column whose correction is not finite or longer
+    than the diagonal solve keeps the diagonal solve), one solve each.  The
+    matrix is generated here (host), copied to the device once per form."""
+    import torch
+    p = synth.WORKLOADS[workload]
+    t0 = time.perf_counter()
+    A = synth.tile_matrix(p["n"], p["nnz_per_row"], seed=p["seed"], fp32=True)
+    t_gen = time.perf_counter() - t0
+    n, k, nnz = A.n, p["k"], A.nnz
+    X0 = synth.initial_guess(A, k, seed=p["seed"] + synth.X0_SEED_OFFSET, fp32=True)
+    out = {"workload": workload, "n": n, "nnz": int(nnz), "k": k, "nev": p["nev"],
+           "generate_s": round(t_gen, 1)}
+    for pc in ("diag", "mlp"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = pkg.from_csr(A, k=k, nev=p["nev"], tol=1e-6, maxiter=1000, precond=pc, polish_fp64=1,
+                         stream=stream, seed=p["seed"])
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        if pc == "diag":
+            with torch.cuda.stream(stream):
+                X = torch.from_numpy(X0).cuda()
+                Y = torch.empty_like(X)
+            for _ in range(3):
+                h.spmm_sym(X, Y)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(11)]
+            for i in range(10):
+                evs[i].record(stream)
+                h.spmm_sym(X, Y)
+                evs[i + 1].record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(evs[i].elapsed_time(evs[i + 1]) for i in range(10))
+            B = alg_bytes(n, nnz, k)
+            out["spmm"] = {"kernel": f"k_spmm_sym_tiled<3, 20> (k={k})", "ms": round(ms, 4),
+                           "alg_bytes_per_launch": int(B), "gbs": round(B / (ms / 1e3) / 1e9, 1),
+                           "frac_of_peak": round(B / (ms / 1e3) / 1e9 / peak_gbs, 4), "traffic": None}
+            h.iterate(3, X0=X)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.iterate(5)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["iteration_ms"] = round(e0.elapsed_time(e1) / 5, 3)
+            del X, Y
+        train = None
+        if pc == "mlp":
+            t0 = time.perf_counter()
+            hist, used = h.precond_train(X0, harvest_iters=20, n_pairs=1 << 20, epochs=5, lr=1e-3)
+            train = {"train_s": round(time.perf_counter() - t0, 3), "pairs": int(used)}
+        t0 = time.perf_counter()
+        try:
+            _, ev, rs, st = h.solve(X0)
+            ok = True
+        except pkg.LobpcgError as e:
+            _, ev, rs, st = e.result
+            ok = False
+        t_solve = time.perf_counter() - t0
+        h.destroy()
+        rec = {"time_to_solution_s": round(t_solve, 3), "create_s": round(t_create, 3), "iters": st["iters"],
+               "iters_fp64": st["iters_fp64"], "converged": bool(ok and st["converged"]),
+               "max_resid": float(np.max(rs)), "evals": [float(v) for v in ev]}
+        if train:
+            rec["training"] = train
+            rec["time_to_solution_with_training_s"] = round(t_solve + train["train_s"], 3)
+        out[pc] = rec
+    if "diag" in out and "mlp" in out:
+        a, b = np.array(out["diag"]["evals"]), np.array(out["mlp"]["evals"])
+        out["forms_agree_max_rel"] = float(np.max(np.abs(a - b) / np.abs(a)))
+    return out
+
+
 def value_only_report(pkg, A, p, stream, spmm_csr_ms: float, peak_gbs: float) -> dict:
     """The SpMM and the diagonal-preconditioned solve with tile_format 1
     (complete 16x16 tiles and complete diagonal triangles keep value words
@@ -392,6 +470,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true")
     ap.add_argument("--solve-repeats", type=int, default=3, help="solves per preconditioner form (median reported)")
+    ap.add_argument("--no-largest", action="store_true", help="skip the n = 8M sub-record")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-value-only", action="store_true")
     ap.add_argument("--fom-only", action="store_true",
@@ -493,6 +572,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A, k)
+    largest = None
+    if rank == 0 and not args.no_largest and not args.no_solves and args.workload == WORKLOAD:
+        del A   # the n = 2M matrix's pinned host copy
+        largest = largest_report(pkg, stream, peaks["hbm_gbs"])
 
     if rank == 0:
         line = {"metric": "symmetric SpMM GB/s", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -511,6 +594,7 @@ def main():
                 "lobpcg": solves,
                 "fom_apply": fom,
                 "value_only_tiles": vonly,
+                "largest": largest,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],
                            "padded_nnz": info["padded_nnz"], "warps": info["warps"]}}
         print(json.dumps(line), flush=True)
