@@ -1602,6 +1602,10 @@ cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, 
     }
     const int64_t ntile = (n + CB_ROWS - 1) / CB_ROWS;
     if constexpr (std::is_same<T, float>::value) {
+        // one output from all inputs, no norms: the bulk-copy kernel (update.cu)
+        if (nout == 1 && out.c0[0] == 0 && out.err && (out.norm_of != 0 || !colsq) &&
+            combine_ff_ok(k, na, a.p, out.z[0]))
+            return launch_combine_ff(n, k, na, a.p, out.C[0], out.z[0], out.err, num_sms, s);
         const bool reg_ok = (nout == 1 || out.c0[1] == k) && out.c0[0] == 0 && out.Cf != nullptr;
         int blocks = static_cast<int>(std::min<int64_t>(ntile, static_cast<int64_t>(num_sms) * 8));
         if (blocks < 1) blocks = 1;

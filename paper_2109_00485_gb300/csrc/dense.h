@@ -22,6 +22,7 @@ struct CombineOut {
     int c0[2];
     int norm_of;
     float *Cf = nullptr;   // device scratch (>= 2 * 96 * 32 floats) for float32 coefficient copies
+    int *err = nullptr;    // device error word: single float32 outputs may take the bulk-copy kernel
 };
 
 template <typename T>
@@ -64,6 +65,20 @@ bool gram_pairs_fit(int k, int nblk, const float *const *blk, int npairs, int un
 // for the bounded waits.
 cudaError_t launch_gram_pairs(int64_t n, int k, int nblk, const float *const *blk, int npairs, const GramPair *pairs,
                               double *M, int ldm, int ldm_rows, bool zero, int *err, int num_sms, cudaStream_t s);
+// update.cu: X <- S C, HX <- HS C, P <- S[:, k:] C[k:], HP <- HS[:, k:] C[k:]
+// and W = R or D_theta^{-1} R (mode 0 / 1) with R = HX - X Theta, in place,
+// plus norms = [||r_j||^2, ||x_j||^2] and colsq = ||p_j||^2 (zeroed here).
+// S, HS: na (2 or 3) float32 n x k blocks, 16-byte aligned; k in {8, 16, 20}.
+// update.cu: Z = [A_0 .. A_{na-1}] C (one float32 output, in place allowed),
+// C (na k) x k FP64; k in {8, 16, 20}, na <= 3, 16-byte aligned blocks.
+bool combine_ff_ok(int k, int na, const float *const *blocks, const float *Z);
+cudaError_t launch_combine_ff(int64_t n, int k, int na, const float *const *A, const double *C, float *Z, int *err,
+                              int num_sms, cudaStream_t s);
+bool update_post_ok(int k, int na, const float *const *blocks);
+cudaError_t launch_update_post(int64_t n, int k, int na, const float *const *S, const float *const *HS,
+                               float *X, float *P, float *HX, float *HP, float *W, const double *C,
+                               const double *theta, const float *d, int mode, double *norms, double *colsq,
+                               int *err, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_combine(int64_t n, int k, int na, GemmBlocks<T> a, int nout, CombineOut<T> out, double *colsq,
                            int num_sms, cudaStream_t s);

@@ -245,12 +245,12 @@ cudaError_t orth_pass(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
     awx.p[0] = b.W;
     awx.p[1] = b.X;
     CombineOut<T> o1{};
-    o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1; o1.Cf = s->Cf;
+    o1.z[0] = b.W; o1.C[0] = s->Cproj; o1.c0[0] = 0; o1.norm_of = -1; o1.Cf = s->Cf; o1.err = h->d_err;
     CK(launch_combine<T>(n, k, 2, awx, 1, o1, nullptr, h->num_sms, h->stream));   // W -= X B
     CK(launch_gram<T>(n, k, 1, aw, 1, aw, s->B, h->num_sms, h->stream, h->d_err));          // B = W^T W
     CK(launch_orth_factor(k, s->B, s->Tm, s->status, h->stream));
     CombineOut<T> o2{};
-    o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1; o2.Cf = s->Cf;
+    o2.z[0] = b.W; o2.C[0] = s->Tm; o2.c0[0] = 0; o2.norm_of = -1; o2.Cf = s->Cf; o2.err = h->d_err;
     return launch_combine<T>(n, k, 1, aw, 1, o2, nullptr, h->num_sms, h->stream);  // W <- W T
 }
 
@@ -279,7 +279,7 @@ cudaError_t orth_pass_pip(lobpcg_ctx *h, SolverState *s, Blocks<T> &b) {
             awx.p[0] = b.W;
             awx.p[1] = b.X;
             CombineOut<T> o{};
-            o.z[0] = b.W; o.C[0] = s->Cproj; o.c0[0] = 0; o.norm_of = -1; o.Cf = s->Cf;
+            o.z[0] = b.W; o.C[0] = s->Cproj; o.c0[0] = 0; o.norm_of = -1; o.Cf = s->Cf; o.err = h->d_err;
             return launch_combine<T>(n, k, 2, awx, 1, o, nullptr, h->num_sms, h->stream);
         }
     }
@@ -404,11 +404,41 @@ cudaError_t gram_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, int na) {
     return launch_gram<T>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err);
 }
 
+// LOBPCG_FUSED_UPDATE=0 keeps the update on the combine kernels and the
+// residual on its own kernel (for comparison).
+bool fused_update_on() {
+    static const bool on = [] {
+        const char *v = std::getenv("LOBPCG_FUSED_UPDATE");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+// Whether body_post forms the next iteration's residual (and W) itself: the
+// fused update kernel (update.cu) takes float32 blocks with k = 8, 16, 20.
+template <typename T>
+bool post_fused(const lobpcg_ctx *h, const SolverState *s, const Blocks<T> &b, bool hasP) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (!fused_update_on()) return false;
+        const int na = hasP ? 3 : 2;
+        const float *S[3] = {b.X, b.W, b.P}, *HS[3] = {b.HX, b.HW, b.HP};
+        const float *blk[6];
+        for (int q = 0; q < na; ++q) {
+            blk[q] = S[q];
+            blk[na + q] = HS[q];
+        }
+        return update_post_ok(s->k, na, blk);
+    } else {
+        (void)h; (void)s; (void)b; (void)hasP;
+        return false;
+    }
+}
+
 // After the SpMM: Gram matrices of S = [X W P], HS = [HX HW HP],
 // Rayleigh-Ritz and the updates X = S C, P = [W P] C_23 (with ||p_j||^2),
 // HX = HS C, HP = [HW HP] C_23.
 template <typename T>
-cudaError_t body_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
+cudaError_t body_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP, int pmode) {
     const int k = s->k;
     const int64_t n = h->T.n;
     const int na = hasP ? 3 : 2;
@@ -423,6 +453,14 @@ cudaError_t body_post(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool hasP) {
     }
     CK(launch_rayleigh_ritz(m, k, 2 * k, s->G, s->G + m, 2 * m, hasP ? s->pscale : nullptr, s->C, s->theta,
                             s->status, h->stream));
+    if constexpr (std::is_same<T, float>::value) {
+        if (post_fused<T>(h, s, b, hasP)) {
+            // updates and the next residual W = K^{-1} R (diagonal K) in one pass
+            const float *S[3] = {b.X, b.W, b.P}, *HS[3] = {b.HX, b.HW, b.HP};
+            return launch_update_post(n, k, na, S, HS, b.X, b.P, b.HX, b.HP, b.W, s->C, s->theta, h->T.diag,
+                                      pmode == 1 ? 1 : 0, s->norms, s->colsqP, h->d_err, h->num_sms, h->stream);
+        }
+    }
     CombineOut<T> ox{}, oh{};
     ox.Cf = s->Cf;
     oh.Cf = s->Cf;
@@ -479,7 +517,7 @@ cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool has
                 if (s->gpost) cudaGraphExecDestroy(s->gpost);
                 s->gpre = s->gpost = nullptr;
                 const bool ok = capture(h, &s->gpre, [&] { return body_pre<T>(h, s, b, pmode, -1); }) &&
-                                capture(h, &s->gpost, [&] { return body_post<T>(h, s, b, true); });
+                                capture(h, &s->gpost, [&] { return body_post<T>(h, s, b, true, pmode); });
                 if (!ok) {
                     s->graph_failed = true;
                     if (s->gpre) cudaGraphExecDestroy(s->gpre);
@@ -498,7 +536,7 @@ cudaError_t iteration_body(lobpcg_ctx *h, SolverState *s, Blocks<T> &b, bool has
     }
     CK(body_pre<T>(h, s, b, pmode, harvest_iter));
     CK(timed_spmm<T>(h, s, b.W, b.HW, k));   // the one SpMM per iteration
-    return body_post<T>(h, s, b, hasP);
+    return body_post<T>(h, s, b, hasP, pmode);
 }
 
 template <typename T>
@@ -521,10 +559,13 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
     int since_best = 0;
     int restarts = 0;
     std::vector<double> rho, theta;
+    bool resid_ready = false;   // the last iteration's fused update formed R (and W)
     while (true) {
         // R = HX - X Theta and norms; W = K^{-1} R
-        CK(launch_resid<T>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
-                           h->stream));
+        if (!resid_ready)
+            CK(launch_resid<T>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms,
+                               h->num_sms, h->stream));
+        resid_ready = false;
         int rr_st = 0, orth_st = 0;
         CK(read_progress<T>(h, s, rho, theta, &rr_st, &orth_st, st));
         trace(std::is_same<T, float>::value ? "fp32" : "fp64", res.iters, rho, theta, nev, rr_st);
@@ -577,6 +618,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
         if (res.iters >= max_iters) break;
         ++res.iters;
         CK(iteration_body<T>(h, s, b, hasP, pmode));
+        resid_ready = post_fused<T>(h, s, b, hasP);
         hasP = true;
     }
     res.rho = rho;
@@ -897,13 +939,16 @@ lobpcg_status iterate(lobpcg_ctx *h, const float *X0, bool x_on_host, int steps,
     }
     std::vector<double> rho, theta;
     const int pmode = harvest ? 2 : h->params.precond;   // harvesting runs the exact tile solves
+    bool resid_ready = false;   // the last iteration's fused update formed R (and W)
     for (int it = 0; it < steps; ++it) {
-        e = launch_resid<float>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms, h->num_sms,
-                                h->stream);
+        if (!resid_ready)
+            e = launch_resid<float>(n, k, b.X, b.HX, s->theta, h->T.diag, b.W, pmode == 1 ? 1 : 0, s->norms,
+                                    h->num_sms, h->stream);
         int rr_st = 0, orth_st = 0;
         if (e == cudaSuccess) e = read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st);
         if (e == cudaSuccess) e = iteration_body<float>(h, s, b, s->hasP32, pmode, harvest ? it : -1);
         if (e != cudaSuccess) return fail(e);
+        resid_ready = post_fused<float>(h, s, b, s->hasP32);
         s->hasP32 = true;
         if (st) st->iters++;
     }

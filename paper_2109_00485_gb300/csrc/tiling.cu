@@ -243,7 +243,11 @@ static cudaError_t build_impl(lobpcg_ctx *h, const int64_t *row_ptr, const int32
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.data), sizeof(uint32_t) * std::max<int64_t>(T.words, 8)));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.chunk), sizeof(ChunkRec) * T.nchunks));
     TRY(dev_alloc(h, reinterpret_cast<void **>(&T.rb_chunk), sizeof(int64_t) * (R + 1)));
-    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.diag), sizeof(float) * n));
+    // padded to a multiple of 4 entries plus 4 (zeros): kernels stage rows of
+    // d by 16-byte bulk copies that may round a ragged last tile up
+    const int64_t n_diag = (n + 3) / 4 * 4 + 4;
+    TRY(dev_alloc(h, reinterpret_cast<void **>(&T.diag), sizeof(float) * n_diag));
+    TRY(cudaMemsetAsync(T.diag, 0, sizeof(float) * n_diag, s));
     int64_t *d_rb_words = nullptr;
     TRY(cudaMallocAsync(&d_rb_words, sizeof(int64_t) * (R + 1), s));
     TRY(cudaMemcpyAsync(T.rb_chunk, rb_chunk.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, s));
