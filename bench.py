@@ -58,8 +58,8 @@ def measured_peaks() -> dict:
     if os.path.exists(p):
         d = json.load(open(p))
         return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
-                "source": "measured"}
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+                "bf16_tflops": float(d.get("bf16_tflops", 1900.0)), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
 def kernel_source_hash() -> str:
@@ -339,6 +339,56 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
     return out
 
 
+def mlp_kernels_report(pkg, stream, peak_tflops: float, rows: int = 500_000, batch: int = 4096) -> dict:
+    """The learned preconditioner's network kernels, timed with CUDA events
+    against the measured dense bf16 peak: the forward pass (129 -> 256 -> 64,
+    bfloat16 tensor-core products, float32 accumulation) on `rows` inputs
+    (one application at n = 2M, k = 16: 31,250 tiles x 16 columns), and the
+    loss with its gradients (forward + backward) on one training batch of
+    `batch` rows.  Algorithmic FLOPs: forward 2 B (129 256 + 256 64);
+    gradients 3 x forward (the two weight gradients and the hidden layer's
+    input gradient are each the size of a forward product)."""
+    import torch
+    A = synth.tile_matrix(256, 20, seed=7, fp32=True)
+    h = pkg.from_csr(A, k=4, nev=1, precond="mlp", stream=stream, seed=7)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    params = (torch.randn(49728, generator=g) * 0.05).numpy().astype(np.float32)
+    h.mlp_set_params(params)
+    with torch.cuda.stream(stream):
+        Xin = torch.randn(rows, 129, device="cuda", dtype=torch.float32)
+        Y = torch.empty(rows, 64, device="cuda", dtype=torch.float32)
+        Xb = Xin[:batch].contiguous()
+        T = torch.randn(batch, 64, device="cuda", dtype=torch.float32)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+    f_ms = timed(lambda: h.mlp_forward(Xin, Y))
+    g_ms = timed(lambda: h.mlp_grad(Xb, T))
+    h.destroy()
+    flop_row = 2.0 * (129 * 256 + 256 * 64)
+    out = {"forward_rows": rows, "forward_ms": round(f_ms, 4), "grad_batch_rows": batch,
+           "grad_ms": round(g_ms, 4),
+           "forward_tflops": round(flop_row * rows / (f_ms / 1e3) / 1e12, 2),
+           "grad_tflops": round(3 * flop_row * batch / (g_ms / 1e3) / 1e12, 2),
+           "peak_bf16_tflops": peak_tflops, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+           "kernel": "k_gemm_bf16 (mma.sync m16n8k16 bf16, float32 accumulation)"}
+    out["forward_frac"] = round(out["forward_tflops"] / peak_tflops, 4)
+    out["grad_frac"] = round(out["grad_tflops"] / peak_tflops, 4)
+    return out
+
+
 def largest_report(pkg, stream, peak_gbs: float, workload: str = "largest_n8m") -> dict:
     """The largest workload (n = 8,000,000, ~250 stored entries per row, about
     2.0 G stored entries, k = 20, nev = 10): the SpMM kernel's time and
@@ -572,6 +622,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A, k)
+    mlpk = None
+    if rank == 0 and not args.no_solves:
+        mlpk = mlp_kernels_report(pkg, stream, peaks["bf16_tflops"])
     largest = None
     if rank == 0 and not args.no_largest and not args.no_solves and args.workload == WORKLOAD:
         del A   # the n = 2M matrix's pinned host copy
@@ -594,6 +647,7 @@ def main():
                 "lobpcg": solves,
                 "fom_apply": fom,
                 "value_only_tiles": vonly,
+                "mlp_kernels": mlpk,
                 "largest": largest,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],
                            "padded_nnz": info["padded_nnz"], "warps": info["warps"]}}

@@ -14,6 +14,7 @@
 // rounded from the FP32 master weights and activations, FP32 accumulation).
 // Training: mean squared error, Adam, on pairs harvested from the solver's
 // own block-Jacobi iterations.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,7 @@ struct GemmArgs {
     int ldc;
     const float *bias;
     int relu;
+    int ksplit = 1;              // CTAs along K: each adds its partial product into C (zeroed first)
 };
 
 constexpr int GT = 64, GK = 32, GPAD = 8;
@@ -64,6 +66,9 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
     __shared__ __align__(16) __nv_bfloat16 As[GT][GK + GPAD];   // [m][k]
     __shared__ __align__(16) __nv_bfloat16 Bs[GT][GK + GPAD];   // [n][k]
     const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    // this CTA's K range (split-K: blockIdx.z of ksplit, in GK steps)
+    const int ksteps = (g.K + GK - 1) / GK, per = (ksteps + g.ksplit - 1) / g.ksplit;
+    const int kbeg = blockIdx.z * per * GK, kend = min(g.K, (blockIdx.z + 1) * per * GK);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int gq = lane >> 2, tq = lane & 3;
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += GK) {
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
         __syncthreads();
         for (int e = threadIdx.x; e < GT * GK; e += blockDim.x) {
             int mm, kk;
@@ -82,7 +87,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
             else { mm = e / GK; kk = e % GK; }            // coalesced along K
             const int gm = m0 + mm, gk = k0 + kk;
             float v = 0.f;
-            if (gm < g.M && gk < g.K) v = g.a_trans ? g.A[static_cast<int64_t>(gk) * g.lda + gm]
+            if (gm < g.M && gk < kend) v = g.a_trans ? g.A[static_cast<int64_t>(gk) * g.lda + gm]
                                                     : g.A[static_cast<int64_t>(gm) * g.lda + gk];
             As[mm][kk] = __float2bfloat16_rn(v);
         }
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
             else { kk = e / GT; nn = e % GT; }
             const int gn = n0 + nn, gk = k0 + kk;
             float v = 0.f;
-            if (gn < g.N && gk < g.K) v = g.b_nk ? g.B[static_cast<int64_t>(gn) * g.ldb + gk]
+            if (gn < g.N && gk < kend) v = g.b_nk ? g.B[static_cast<int64_t>(gn) * g.ldb + gk]
                                                  : g.B[static_cast<int64_t>(gk) * g.ldb + gn];
             Bs[nn][kk] = __float2bfloat16_rn(v);
         }
@@ -130,15 +135,32 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
                 const int col = n0 + wn + 8 * b + 2 * tq + (c & 1);
                 if (r < g.M && col < g.N) {
                     float v = acc[a][b][c];
-                    if (g.bias) v += g.bias[col];
-                    if (g.relu) v = fmaxf(v, 0.f);
-                    g.C[static_cast<int64_t>(r) * g.ldc + col] = v;
+                    if (g.ksplit > 1) {
+                        atomicAdd(&g.C[static_cast<int64_t>(r) * g.ldc + col], v);
+                    } else {
+                        if (g.bias) v += g.bias[col];
+                        if (g.relu) v = fmaxf(v, 0.f);
+                        g.C[static_cast<int64_t>(r) * g.ldc + col] = v;
+                    }
                 }
             }
 }
 
-static cudaError_t gemm(const GemmArgs &g, cudaStream_t s) {
-    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT);
+static cudaError_t gemm(const GemmArgs &g0, cudaStream_t s, int num_sms = 0) {
+    GemmArgs g = g0;
+    const int tiles = ((g.N + GT - 1) / GT) * ((g.M + GT - 1) / GT);
+    // a long reduction (the weight gradients: K = batch rows) over few output
+    // tiles is split along K so that about two CTAs per SM run it
+    g.ksplit = 1;
+    if (num_sms > 0 && !g.bias && !g.relu && tiles < num_sms) {
+        const int ksteps = (g.K + GT - 1) / GT;
+        g.ksplit = std::max(1, std::min(ksteps / 2, (2 * num_sms + tiles - 1) / tiles));
+    }
+    if (g.ksplit > 1) {   // C is accumulated into: zero it (rows of N floats, stride ldc)
+        const cudaError_t e = cudaMemset2DAsync(g.C, sizeof(float) * g.ldc, 0, sizeof(float) * g.N, g.M, s);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.ksplit);
     k_gemm_bf16<<<grid, 128, 0, s>>>(g);
     return cudaGetLastError();
 }
@@ -332,19 +354,25 @@ __global__ void k_mlp_relu_bwd(int64_t m, const float *H, float *dH) {
         if (!(H[e] > 0.f)) dH[e] = 0.f;
 }
 
-// db[c] = sum over rows of D[r][c]   (D: B x N)
+// db[c] += sum over rows of D[r][c]   (D: B x N, N <= blockDim; db zeroed
+// first): each CTA sums a range of rows for all N columns (thread c reads
+// column c: rows are read whole, coalesced), one atomic per column and CTA.
 __global__ void k_mlp_colsum(int64_t B, int N, const float *D, float *db) {
-    const int c = blockIdx.x;
+    const int c = threadIdx.x;
+    if (c >= N) return;
+    const int64_t per = (B + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * per, r1 = min(B, r0 + per);
     float acc = 0.f;
-    for (int64_t r = threadIdx.x; r < B; r += blockDim.x) acc += D[r * N + c];
-    __shared__ float red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[c] = red[0];
+    for (int64_t r = r0; r < r1; ++r) acc += D[r * N + c];
+    atomicAdd(&db[c], acc);
+}
+
+static cudaError_t colsum(int64_t B, int N, const float *D, float *db, int num_sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(db, 0, sizeof(float) * N, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2 * num_sms, (B + 63) / 64)));
+    k_mlp_colsum<<<blocks, N <= 64 ? 64 : 256, 0, s>>>(B, N, D, db);
+    return cudaGetLastError();
 }
 
 // Adam (Kingma & Ba 2015), bias-corrected, over the packed parameters.
@@ -487,8 +515,8 @@ static cudaError_t backward(lobpcg_ctx *h, const float *X, const float *T, int64
     // dW2 = dY^T H  (64 x 256)
     GemmArgs gw2{MLP_NOUT, MLP_NHID, static_cast<int>(B), dY, MLP_NOUT, 1, Hh, MLP_NHID, 0, M.G + MLP_OFF_W2,
                  MLP_NHID, nullptr, 0};
-    if ((e = gemm(gw2, h->stream)) != cudaSuccess) return e;
-    k_mlp_colsum<<<MLP_NOUT, 256, 0, h->stream>>>(B, MLP_NOUT, dY, M.G + MLP_OFF_B2);
+    if ((e = gemm(gw2, h->stream, h->num_sms)) != cudaSuccess) return e;
+    if ((e = colsum(B, MLP_NOUT, dY, M.G + MLP_OFF_B2, h->num_sms, h->stream)) != cudaSuccess) return e;
     // dH = (dY W2) * relu'
     GemmArgs gh{static_cast<int>(B), MLP_NHID, MLP_NOUT, dY, MLP_NOUT, 0, M.P + MLP_OFF_W2, MLP_NHID, 0, dH, MLP_NHID,
                 nullptr, 0};
@@ -497,9 +525,8 @@ static cudaError_t backward(lobpcg_ctx *h, const float *X, const float *T, int64
     // dW1 = dH^T X  (256 x 144)
     GemmArgs gw1{MLP_NHID, MLP_KIN, static_cast<int>(B), dH, MLP_NHID, 1, X, MLP_KIN, 0, M.G + MLP_OFF_W1, MLP_KIN,
                  nullptr, 0};
-    if ((e = gemm(gw1, h->stream)) != cudaSuccess) return e;
-    k_mlp_colsum<<<MLP_NHID, 256, 0, h->stream>>>(B, MLP_NHID, dH, M.G + MLP_OFF_B1);
-    return cudaGetLastError();
+    if ((e = gemm(gw1, h->stream, h->num_sms)) != cudaSuccess) return e;
+    return colsum(B, MLP_NHID, dH, M.G + MLP_OFF_B1, h->num_sms, h->stream);
 }
 
 cudaError_t mlp_forward_rows(lobpcg_ctx *h, const float *X129, int64_t B, float *Y) {
