@@ -129,11 +129,12 @@ class ClockSampler:
 
 
 # Kernel launches of one LOBPCG iteration with a P block (from the ncu launch
-# list of this bench): residual; first orthonormalisation pass (2 Gram,
-# projection coefficients, Cholesky-QR factor, 2 casts, 2 combines); second
-# pass (Gram, Omega, factor, coefficients, cast, combine); SpMM; Gram,
-# P scaling, Rayleigh-Ritz, 2 x (cast, combine) = 23.
-LAUNCHES_PER_ITERATION = 23
+# list of this bench, profiles/spmm_sym_full_n2m_ncu.md): first
+# orthonormalisation pass (2 Gram, projection coefficients, Cholesky-QR
+# factor, 2 combines); second pass (Gram, Omega, factor, coefficients,
+# combine); SpMM; Gram, P scaling, Rayleigh-Ritz; the fused update with the
+# next residual = 16.
+LAUNCHES_PER_ITERATION = 16
 
 
 def aggregate(total_ms: float, bytes_per_step: int, steps: int, world: int, device=None):
