@@ -246,12 +246,12 @@ struct LcArgs {
     int *err;
 };
 
-template <int K>
+template <int K, int NA>
 __global__ void __launch_bounds__(UP_THREADS, 1) k_combine_ff(const __grid_constant__ LcArgs a) {
     extern __shared__ __align__(16) float lc_smem[];
     __shared__ __align__(8) uint64_t full[UP_MAXSTAGES], empty[UP_MAXSTAGES];
     __shared__ int abort_flag;
-    const int NS = a.stages, NA = a.na, TR = a.rows_t;
+    const int NS = a.stages, TR = a.rows_t;
     const int TILE_F = TR * K;
     const int stage_f = NA * TILE_F;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,9 +302,13 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_combine_ff(const __grid_const
         constexpr int G = (UP_CONS * 32) / K;
         const int j = ct % K, g = ct / K;
         const bool act = g < G;
-        float c[3 * K];
+        float c[NA * K];
 #pragma unroll
-        for (int q = 0; q < 3 * K; ++q) c[q] = (q < NA * K) ? static_cast<float>(a.C[q * K + j]) : 0.f;
+        for (int q = 0; q < NA * K; ++q) c[q] = static_cast<float>(a.C[q * K + j]);
+        // rows per step: every row's 4-vectors are loaded before any FMA, so
+        // a thread has RPS independent chains in flight (the loop is bound by
+        // the shared-load latency otherwise)
+        constexpr int RPS = NA == 1 ? 4 : (NA == 2 ? 2 : 1);
         bool bad = false;
         for (int i = 0; i < my_tiles; ++i) {
             const int s = i % NS;
@@ -318,25 +322,30 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_combine_ff(const __grid_const
             const float *st = lc_smem + s * stage_f;
             if (act) {
 #pragma unroll 1
-                for (int r = g; r < rows; r += G) {
-                    float za[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int r = g; r < rows; r += RPS * G) {
+                    float4 v[RPS][NA * (K / 4)];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q >= NA) continue;
-                        float4 v[K / 4];
-                        const float4 *sr = reinterpret_cast<const float4 *>(st + q * TILE_F + r * K);
+                    for (int u = 0; u < RPS; ++u) {
+                        const int ru = r + u * G < rows ? r + u * G : r;   // past the tile: reload row r
 #pragma unroll
-                        for (int c4 = 0; c4 < K / 4; ++c4) v[c4] = sr[c4];
+                        for (int q = 0; q < NA; ++q) {
+                            const float4 *sr = reinterpret_cast<const float4 *>(st + q * TILE_F + ru * K);
 #pragma unroll
-                        for (int c4 = 0; c4 < K / 4; ++c4) {
-                            const int cc = q * K + 4 * c4;
-                            za[0] = fmaf(v[c4].x, c[cc], za[0]);
-                            za[1] = fmaf(v[c4].y, c[cc + 1], za[1]);
-                            za[2] = fmaf(v[c4].z, c[cc + 2], za[2]);
-                            za[3] = fmaf(v[c4].w, c[cc + 3], za[3]);
+                            for (int c4 = 0; c4 < K / 4; ++c4) v[u][q * (K / 4) + c4] = sr[c4];
                         }
                     }
-                    a.Z[(r0 + r) * K + j] = (za[0] + za[1]) + (za[2] + za[3]);
+#pragma unroll
+                    for (int u = 0; u < RPS; ++u) {
+                        float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+                        for (int c4 = 0; c4 < NA * (K / 4); ++c4) {
+                            z0 = fmaf(v[u][c4].x, c[4 * c4], z0);
+                            z1 = fmaf(v[u][c4].y, c[4 * c4 + 1], z1);
+                            z0 = fmaf(v[u][c4].z, c[4 * c4 + 2], z0);
+                            z1 = fmaf(v[u][c4].w, c[4 * c4 + 3], z1);
+                        }
+                        if (r + u * G < rows) a.Z[(r0 + r + u * G) * K + j] = z0 + z1;
+                    }
                 }
             }
             __syncwarp();
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_combine_ff(const __grid_const
     }
 }
 
-template <int K>
+template <int K, int NA>
 cudaError_t launch_lc(const LcArgs &a0, int num_sms, cudaStream_t s) {
     LcArgs a = a0;
     // about 48 KB of inputs per tile (a multiple of the row groups so full
@@ -362,14 +371,14 @@ cudaError_t launch_lc(const LcArgs &a0, int num_sms, cudaStream_t s) {
     const size_t smem = a.stages * stage_bytes;
     static bool attr = false;
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_combine_ff<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        const cudaError_t e = cudaFuncSetAttribute(k_combine_ff<K, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int64_t ntile = (a.n + a.rows_t - 1) / a.rows_t;
     const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ntile, num_sms)));
-    k_combine_ff<K><<<blocks, UP_THREADS, smem, s>>>(a);
+    k_combine_ff<K, NA><<<blocks, UP_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -412,10 +421,16 @@ cudaError_t launch_combine_ff(int64_t n, int k, int na, const float *const *A, c
     a.Z = Z;
     a.C = C;
     a.err = err;
-    switch (k) {
-        case 8: return launch_lc<8>(a, num_sms, s);
-        case 16: return launch_lc<16>(a, num_sms, s);
-        case 20: return launch_lc<20>(a, num_sms, s);
+    switch (k * 4 + na) {
+        case 8 * 4 + 1: return launch_lc<8, 1>(a, num_sms, s);
+        case 8 * 4 + 2: return launch_lc<8, 2>(a, num_sms, s);
+        case 8 * 4 + 3: return launch_lc<8, 3>(a, num_sms, s);
+        case 16 * 4 + 1: return launch_lc<16, 1>(a, num_sms, s);
+        case 16 * 4 + 2: return launch_lc<16, 2>(a, num_sms, s);
+        case 16 * 4 + 3: return launch_lc<16, 3>(a, num_sms, s);
+        case 20 * 4 + 1: return launch_lc<20, 1>(a, num_sms, s);
+        case 20 * 4 + 2: return launch_lc<20, 2>(a, num_sms, s);
+        case 20 * 4 + 3: return launch_lc<20, 3>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
