@@ -126,6 +126,21 @@ __device__ __forceinline__ void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// d + a * b on two packed floats, lane by lane (fma.rn.f32x2: two FP32
+// FMAs, each rounded once as fmaf, in one instruction).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 d) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rd, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(d.x), "f"(d.y));
+    return r;
+}
+
 // y[0..3] += v[0..3] as one vector reduction in L2 (sm_90+).
 __device__ __forceinline__ void red_add_v4(float *y, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(a), "f"(b), "f"(c), "f"(d)

@@ -93,13 +93,21 @@ __device__ __forceinline__ bool unit_of(const GfArgs &a, int u, int &p, int &si,
     return false;
 }
 
-// part[4 i + j] += x_i y_j
+// part[4 i + j] += x_i y_j, as packed pairs (x_i, x_i) (y_0, y_1) and
+// (x_i, x_i) (y_2, y_3): eight fma.rn.f32x2 for the sixteen products
 __device__ __forceinline__ void fma16(float (&part)[16], const float4 x, const float4 y) {
-    const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+    const float xv[4] = {x.x, x.y, x.z, x.w};
+    const float2 y01 = make_float2(y.x, y.y), y23 = make_float2(y.z, y.w);
 #pragma unroll
-    for (int i2 = 0; i2 < 4; ++i2)
-#pragma unroll
-        for (int j2 = 0; j2 < 4; ++j2) part[i2 * 4 + j2] = fmaf(xv[i2], yv[j2], part[i2 * 4 + j2]);
+    for (int i2 = 0; i2 < 4; ++i2) {
+        const float2 xx = make_float2(xv[i2], xv[i2]);
+        float2 a = fma2(xx, y01, make_float2(part[i2 * 4], part[i2 * 4 + 1]));
+        float2 b = fma2(xx, y23, make_float2(part[i2 * 4 + 2], part[i2 * 4 + 3]));
+        part[i2 * 4] = a.x;
+        part[i2 * 4 + 1] = a.y;
+        part[i2 * 4 + 2] = b.x;
+        part[i2 * 4 + 3] = b.y;
+    }
 }
 
 // Warp 0 is the producer (lane 0 issues the bulk copies of each tile into a

@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_update_post(const __grid_cons
                 for (int r = g; r < rows; r += G) {
                     // the S and HS rows block by block, P blocks first (p is
                     // the partial sum of x), each block's 4-vectors loaded
-                    // before its FMAs
-                    float p = 0.f, hp = 0.f;
+                    // before its FMAs; packed pairs (even and odd columns)
+                    float2 p2 = make_float2(0.f, 0.f), hp2 = p2;
 #pragma unroll
                     for (int q = 1; q < NA; ++q) {
                         float4 v[K / 4], w[K / 4];
@@ -156,17 +156,15 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_update_post(const __grid_cons
 #pragma unroll
                         for (int c4 = 0; c4 < K / 4; ++c4) {
                             const int cc = q * K + 4 * c4;
-                            p = fmaf(v[c4].x, c[cc], p);
-                            hp = fmaf(w[c4].x, c[cc], hp);
-                            p = fmaf(v[c4].y, c[cc + 1], p);
-                            hp = fmaf(w[c4].y, c[cc + 1], hp);
-                            p = fmaf(v[c4].z, c[cc + 2], p);
-                            hp = fmaf(w[c4].z, c[cc + 2], hp);
-                            p = fmaf(v[c4].w, c[cc + 3], p);
-                            hp = fmaf(w[c4].w, c[cc + 3], hp);
+                            const float2 c01 = make_float2(c[cc], c[cc + 1]), c23 = make_float2(c[cc + 2], c[cc + 3]);
+                            p2 = fma2(make_float2(v[c4].x, v[c4].y), c01, p2);
+                            hp2 = fma2(make_float2(w[c4].x, w[c4].y), c01, hp2);
+                            p2 = fma2(make_float2(v[c4].z, v[c4].w), c23, p2);
+                            hp2 = fma2(make_float2(w[c4].z, w[c4].w), c23, hp2);
                         }
                     }
-                    float x = p, hx = hp;
+                    const float p = p2.x + p2.y, hp = hp2.x + hp2.y;
+                    float2 x2 = make_float2(p, 0.f), hx2 = make_float2(hp, 0.f);
                     {
                         float4 v[K / 4], w[K / 4];
                         const float4 *sr = reinterpret_cast<const float4 *>(st + r * K);
@@ -178,16 +176,14 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_update_post(const __grid_cons
 #pragma unroll
                         for (int c4 = 0; c4 < K / 4; ++c4) {
                             const int cc = 4 * c4;
-                            x = fmaf(v[c4].x, c[cc], x);
-                            hx = fmaf(w[c4].x, c[cc], hx);
-                            x = fmaf(v[c4].y, c[cc + 1], x);
-                            hx = fmaf(w[c4].y, c[cc + 1], hx);
-                            x = fmaf(v[c4].z, c[cc + 2], x);
-                            hx = fmaf(w[c4].z, c[cc + 2], hx);
-                            x = fmaf(v[c4].w, c[cc + 3], x);
-                            hx = fmaf(w[c4].w, c[cc + 3], hx);
+                            const float2 c01 = make_float2(c[cc], c[cc + 1]), c23 = make_float2(c[cc + 2], c[cc + 3]);
+                            x2 = fma2(make_float2(v[c4].x, v[c4].y), c01, x2);
+                            hx2 = fma2(make_float2(w[c4].x, w[c4].y), c01, hx2);
+                            x2 = fma2(make_float2(v[c4].z, v[c4].w), c23, x2);
+                            hx2 = fma2(make_float2(w[c4].z, w[c4].w), c23, hx2);
                         }
                     }
+                    const float x = x2.x + x2.y, hx = hx2.x + hx2.y;
                     const int64_t e = (r0 + r) * K + j;
                     const float res = hx - x * th;
                     float w = res;
@@ -336,15 +332,14 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_combine_ff(const __grid_const
                     }
 #pragma unroll
                     for (int u = 0; u < RPS; ++u) {
-                        float z0 = 0.f, z1 = 0.f;
+                        // packed pairs: (v.x, v.y) (c0, c1) and (v.z, v.w) (c2, c3)
+                        float2 z = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int c4 = 0; c4 < NA * (K / 4); ++c4) {
-                            z0 = fmaf(v[u][c4].x, c[4 * c4], z0);
-                            z1 = fmaf(v[u][c4].y, c[4 * c4 + 1], z1);
-                            z0 = fmaf(v[u][c4].z, c[4 * c4 + 2], z0);
-                            z1 = fmaf(v[u][c4].w, c[4 * c4 + 3], z1);
+                            z = fma2(make_float2(v[u][c4].x, v[u][c4].y), make_float2(c[4 * c4], c[4 * c4 + 1]), z);
+                            z = fma2(make_float2(v[u][c4].z, v[u][c4].w), make_float2(c[4 * c4 + 2], c[4 * c4 + 3]), z);
                         }
-                        if (r + u * G < rows) a.Z[(r0 + r + u * G) * K + j] = z0 + z1;
+                        if (r + u * G < rows) a.Z[(r0 + r + u * G) * K + j] = z.x + z.y;
                     }
                 }
             }
