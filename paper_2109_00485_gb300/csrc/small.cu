@@ -172,19 +172,19 @@ __device__ void cta_trsm_rows(const double *L, const double *rd, double *B, int 
     __syncthreads();
 }
 
-// Y <- L^{-T} Y (Y m x nc, row stride nc): back substitution, right-looking
+// Y <- L^{-T} Y (Y m x nc, row stride ldy): back substitution, right-looking
 // from the last row, same conventions as cta_trsm_rows.
-__device__ void cta_trsm_rows_t(const double *L, const double *rd, double *Y, int m, int nc) {
+__device__ void cta_trsm_rows_t(const double *L, const double *rd, double *Y, int m, int nc, int ldy) {
     const int per = blockDim.x / nc;
     const int c = threadIdx.x % nc, r0 = threadIdx.x / nc;
     for (int i = m - 1; i > 0; --i) {
         if (r0 < per) {
-            const double ci = Y[i * nc + c] * rd[i];
-            for (int r = r0; r < i; r += per) Y[r * nc + c] = fma(-L[i * m + r], ci, Y[r * nc + c]);
+            const double ci = Y[i * ldy + c] * rd[i];
+            for (int r = r0; r < i; r += per) Y[r * ldy + c] = fma(-L[i * m + r], ci, Y[r * ldy + c]);
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) Y[e] *= rd[e / nc];
+    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) Y[(e / nc) * ldy + e % nc] *= rd[e / nc];
     __syncthreads();
 }
 
@@ -296,150 +296,169 @@ __device__ int cta_jacobi(double *A, double *V, int m, double *cs, int *pairs, i
 }
 
 // The k smallest eigenpairs of the symmetric m x m matrix A (shared memory,
-// lower triangle used, destroyed), FP64, one CTA of at least 128 threads
-// (m <= 96, k <= 32):
+// lower triangle used, destroyed), FP64, one CTA of 256 threads (m <= 96,
+// k <= 32):
 //   1. Householder tridiagonalisation A = Q T Q^T (Golub & Van Loan,
-//      Section 8.3.1), updating the lower triangle only; the reflectors stay
-//      in A's lower triangle.
-//   2. Eigenvalue brackets of T / ||T|| by float32 multisection on the Sturm
-//      count (the number of negative pivots of T - x I): one warp per
-//      eigenvalue, 32 points per step.
+//      Section 8.3.1) on the lower triangle.  Per column: warp 0 forms the
+//      reflector while the other warps compute y = A22 x with the unscaled
+//      column x (v = s (x - alpha e1) and p = tau A22 v = tau s (y - alpha
+//      A22 e1), v^T p from x^T y, y_0 and A22[0][0]), then w = p - (tau/2)
+//      (v^T p) v and the rank-2 update A22 -= v w^T + w v^T.  Reflector j is
+//      kept in row j of A's (unused) upper triangle.
+//   2. Eigenvalue brackets of T / ||T|| by float32 Sturm counts (the number
+//      of negative pivots of T - x I): 256 points over [-1, 1], then each
+//      bracket narrowed by 8-32 points per step on its own lanes.
 //   3. float64 bisection of the brackets to 1e-10 ||T||: four warps (one per
-//      sub-partition), 128 / k points per eigenvalue, with the Sturm count as
-//      the sign changes of the leading principal minors p_r of T - x I
+//      sub-partition), 4-16 points per eigenvalue, the Sturm count being the
+//      sign changes of the leading principal minors p_r of T - x I
 //      (p_{r+1} = (d_r - x) p_r - e_{r-1}^2 p_{r-1}: no division).
-//   4. Eigenvector by two steps of inverse iteration with T - w_i I
-//      (tridiagonal LU with partial pivoting), one lane per pair, the pairs
-//      spread over four warps; the eigenvalue is then the Rayleigh quotient.
-//      Vectors of eigenvalues closer than 1e-10 ||T|| are re-orthogonalised.
-//   5. Back-transformation by the reflectors, V = Q Y, one warp per group of
-//      columns (no barrier between reflectors).
-// Outputs: w[0..k) ascending, V (m x k, row-major, shared memory).
+//   4. Eigenvectors by two steps of inverse iteration with T - w_i I
+//      (tridiagonal LU with partial pivoting), all pairs on the lanes of one
+//      warp; norms and Rayleigh quotients (the eigenvalues returned) over
+//      the rows on four warps.  Vectors of eigenvalues closer than
+//      1e-10 ||T|| are re-orthogonalised.
+//   5. Back-transformation by the reflectors, V = Q Y, four warps each
+//      owning a group of columns (no barrier between reflectors).
+// Outputs: w[0..k) ascending, V (m x k, row stride ldv, shared memory).
+// wk: shared scratch of 3 * EIG_MAXM doubles; y: EIG_MAXM doubles.
 constexpr int EIG_MAXM = 96;
+constexpr int EIG_THREADS = 256;
 
-// Step 5 of cta_eigh_smallest for one warp: columns c = warp + 4 cl of V,
-// rows r = rg + RG t (t < NR), lane = cl RG + rg.
-template <int NR>
-__device__ __forceinline__ void back_transform(const double *A, const double *tau, double *V, int m, int k, int warp,
-                                               int lane, int RG, int ncol) {
-    const int cl = lane / RG, rg = lane % RG;
-    const int c = warp + 4 * cl;
-    const bool colok = cl < ncol;
-    double vc[NR];
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        const int r = rg + RG * t;
-        vc[t] = (colok && r < m) ? V[r * k + c] : 0.0;
+// Folded enumeration of the lower triangle (diagonal included) of an n x n
+// block: folded row q holds rows q and n - 1 - q (n + 1 entries), entry
+// e = q (n + 1) + c.  Returns false for the repeated half of the middle row
+// of an odd n.  Consecutive e are consecutive columns of one row.
+__device__ __forceinline__ bool tri_fold(int e, int n, int &a, int &b) {
+    const int q = e / (n + 1), c = e - q * (n + 1);
+    if (c <= q) {
+        a = q;
+        b = c;
+        return true;
     }
-    for (int j = m - 3; j >= 0; --j) {
-        const double tj = tau[j];
-        if (tj == 0.0) continue;
-        double dot = 0.0;
-#pragma unroll
-        for (int t = 0; t < NR; ++t) {
-            const int r = rg + RG * t;
-            if (r > j && r < m) dot = fma(A[r * m + j], vc[t], dot);
-        }
-        for (int o = 1; o < RG; o <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        dot *= tj;
-#pragma unroll
-        for (int t = 0; t < NR; ++t) {
-            const int r = rg + RG * t;
-            if (r > j && r < m) vc[t] = fma(-dot, A[r * m + j], vc[t]);
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        const int r = rg + RG * t;
-        if (colok && r < m) V[r * k + c] = vc[t];
-    }
+    a = n - 1 - q;
+    b = c - q - 1;
+    return a > q;
 }
 
-__device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V, double *d, double *e,
-                                  double *tau, double *pv) {
-    __shared__ double red_s, tnorm, tau_s;
-    __shared__ double blo[32], bhi[32], e2[EIG_MAXM], sv[EIG_MAXM], sw[EIG_MAXM];
-    __shared__ float df[EIG_MAXM], e2f[EIG_MAXM];
+// Step 1 of cta_eigh_smallest.  d[0..m), e[0..m-1), tau[0..m-2) out;
+// reflector j (v_{j+1} = 1) in A[j][j+1 .. m-1].
+__device__ void cta_tridiag(double *A, int m, double *d, double *e, double *tau, double *sx, double *sy, double *sv,
+                            double *sw) {
+    __shared__ double scal[4];   // tau_j, s_j (v = s_j (x - alpha e1)), alpha_j, K_j
+    __shared__ double sred[EIG_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // 1. tridiagonalisation
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sx[i] = A[i * m];
+    __syncthreads();
     for (int j = 0; j + 2 < m; ++j) {
+        const int b0 = j + 1, nt = m - b0;
         if (warp == 0) {
+            // reflector of x = A[b0.., j]: alpha = -sign(x0) mu, tau = 1 + |x0| / mu,
+            // s = 1 / (x0 - alpha)
             double sg = 0.0;
-            for (int i = j + 2 + lane; i < m; i += 32) sg = fma(A[i * m + j], A[i * m + j], sg);
+            for (int i = b0 + 1 + lane; i < m; i += 32) sg = fma(sx[i], sx[i], sg);
             sg = warp_sum_d(sg);
             if (lane == 0) {
-                const double x0 = A[(j + 1) * m + j];
+                const double x0 = sx[b0];
                 d[j] = A[j * m + j];
                 if (sg == 0.0) {
-                    tau_s = 0.0;
+                    scal[0] = 0.0;
                     e[j] = x0;
                 } else {
-                    // alpha = -sign(x0) mu, v = x - alpha e_1 scaled to v_0 = 1,
-                    // tau = 2 / (v^T v) = 1 + |x0| / mu, 1 / v_0 by Newton steps
                     const double s2 = fma(x0, x0, sg);
                     const double r = rsqrt64(s2);
                     const double mu = s2 * r;
                     const double alpha = (x0 <= 0.0) ? mu : -mu;
-                    tau_s = fma(fabs(x0), r, 1.0);
-                    red_s = rcp64(x0 - alpha);
+                    scal[0] = fma(fabs(x0), r, 1.0);
+                    scal[1] = rcp64(x0 - alpha);
+                    scal[2] = alpha;
                     e[j] = alpha;
                 }
             }
+        } else {
+            // y = A22 x: four lanes per row (columns b0 + part + 4 t), the
+            // starting t rotated by the row so that the four rows of a
+            // half-warp read different banks; x^T y summed per warp
+            const int part = lane & 3, rq = lane >> 2;
+            const int T = (nt + 3) >> 2;
+            const int rot = (m & 3) ? rq : ((rq * (1 - (m >> 2))) & 3);
+            double cxy = 0.0;
+            for (int r0 = (warp - 1) * 8; r0 < nt; r0 += (nwarps - 1) * 8) {
+                const int i = b0 + r0 + rq;
+                const bool act = i < m;
+                double a0 = 0.0, a1 = 0.0;
+                if (act) {
+                    int t = rot % T;
+                    for (int u = 0; u < T; ++u) {
+                        const int l = b0 + part + 4 * t;
+                        if (l < m) {
+                            const double a = (l <= i) ? A[i * m + l] : A[l * m + i];
+                            if (u & 1) a1 = fma(a, sx[l], a1);
+                            else a0 = fma(a, sx[l], a0);
+                        }
+                        if (++t == T) t = 0;
+                    }
+                }
+                double acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (act) {
+                    if (part == 0) sy[i] = acc;
+                    cxy = fma(sx[i], acc, cxy);
+                }
+            }
+            // one copy per row (lanes of a row hold the same value)
+            cxy += __shfl_xor_sync(0xffffffffu, cxy, 4);
+            cxy += __shfl_xor_sync(0xffffffffu, cxy, 8);
+            cxy += __shfl_xor_sync(0xffffffffu, cxy, 16);
+            if (lane == 0) sred[warp] = cxy;
         }
         __syncthreads();
-        const double tj = tau_s;
-        tau[j] = tj;   // every thread writes the same value
-        if (tj == 0.0) {
-            if (threadIdx.x == 0) A[(j + 1) * m + j] = 1.0;
+        const double tj = scal[0];
+        if (tj == 0.0) {   // x = x0 e1 already: H_j = I
+            if (threadIdx.x == 0) tau[j] = 0.0;
+            for (int i = b0 + 1 + threadIdx.x; i < m; i += blockDim.x) sx[i] = A[i * m + b0];
             __syncthreads();
             continue;
         }
-        const double rs = red_s;
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-            const double v = (i == j + 1) ? 1.0 : A[i * m + j] * rs;
-            A[i * m + j] = v;
-            sv[i] = v;
-        }
-        __syncthreads();
-        // p = tau A22 v, four threads per row (A22 read through its lower triangle)
-        const int nt = m - j - 1;
-        const int qend = (4 * nt + 31) & ~31;   // whole warps, so the shuffles see every lane
-        for (int q = threadIdx.x; q < qend; q += blockDim.x) {
-            const bool act = q < 4 * nt;
-            const int i = j + 1 + (q >> 2), part = q & 3;
-            double a0 = 0.0, a1 = 0.0;
-            if (act) {
-                int l = j + 1 + part;
-                for (; l + 4 < m; l += 8) {
-                    const double m0 = (l <= i) ? A[i * m + l] : A[l * m + i];
-                    const double m1 = (l + 4 <= i) ? A[i * m + l + 4] : A[(l + 4) * m + i];
-                    a0 = fma(m0, sv[l], a0);
-                    a1 = fma(m1, sv[l + 4], a1);
-                }
-                if (l < m) a0 = fma((l <= i) ? A[i * m + l] : A[l * m + i], sv[l], a0);
-            }
-            double acc = a0 + a1;
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (act && part == 0) pv[i] = tj * acc;
-        }
-        __syncthreads();
-        // K = tau v^T p / 2, w = p - K v
+        const double sj = scal[1], alpha = scal[2];
         if (warp == 0) {
-            double kk = 0.0;
-            for (int l = j + 1 + lane; l < m; l += 32) kk = fma(sv[l], pv[l], kk);
-            kk = warp_sum_d(kk);
-            const double K = 0.5 * tj * kk;
-            for (int l = j + 1 + lane; l < m; l += 32) sw[l] = fma(-K, sv[l], pv[l]);
+            // v^T p = tau s^2 (x^T y - 2 alpha y_0 + alpha^2 A22[0][0]), K = tau v^T p / 2
+            double c = (lane >= 1 && lane < nwarps) ? sred[lane] : 0.0;
+            c += __shfl_xor_sync(0xffffffffu, c, 1);
+            c += __shfl_xor_sync(0xffffffffu, c, 2);
+            c += __shfl_xor_sync(0xffffffffu, c, 4);
+            if (lane == 0) {
+                const double q = fma(alpha, fma(alpha, A[b0 * m + b0], -2.0 * sy[b0]), c);
+                const double ts = tj * sj;
+                scal[3] = 0.5 * (ts * ts) * q;
+                tau[j] = tj;
+            }
+        } else {
+            // v and p = tau s (y - alpha A22 e1); v also into row j (reflector)
+            const double ts = tj * sj;
+            for (int i = b0 + threadIdx.x - 32; i < m; i += blockDim.x - 32) {
+                const double vi = (i == b0) ? 1.0 : sj * sx[i];
+                sv[i] = vi;
+                A[j * m + i] = vi;
+                sw[i] = ts * fma(-alpha, A[i * m + b0], sy[i]);
+            }
         }
         __syncthreads();
-        // A22 -= v w^T + w v^T (lower triangle including the diagonal)
-        const int cnt = nt * (nt + 1) / 2;
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            int r1, c1;
-            tri_rc(q, r1, c1);
-            const int i = j + r1, l = j + 1 + c1;
-            A[i * m + l] -= fma(sv[i], sw[l], sw[i] * sv[l]);
+        {
+            const double K = scal[3];
+            for (int i = b0 + threadIdx.x; i < m; i += blockDim.x) sw[i] = fma(-K, sv[i], sw[i]);
+        }
+        __syncthreads();
+        // A22 -= v w^T + w v^T on the lower triangle; column b0 below the
+        // diagonal is the next x
+        const int tot = ((nt + 1) >> 1) * (nt + 1);
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            int a, b;
+            if (!tri_fold(q, nt, a, b)) continue;
+            const int i = b0 + a, l = b0 + b;
+            const double val = fma(-sv[i], sw[l], fma(-sw[i], sv[l], A[i * m + l]));
+            A[i * m + l] = val;
+            if (b == 0 && a > 0) sx[i] = val;
         }
         __syncthreads();
     }
@@ -450,15 +469,50 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             if (m >= 3) tau[m - 2] = 0.0;
         }
         d[m - 1] = A[(m - 1) * m + (m - 1)];
-        double tn = 0.0;
-        for (int i = 0; i < m; ++i) {
-            const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
-            tn = fmax(tn, r);
-        }
-        tnorm = (tn > 0.0) ? tn : 1.0;
     }
     __syncthreads();
-    // T / ||T||: diagonal d / ||T||, squared off-diagonal e^2 / ||T||^2
+}
+
+// Keeps the minor recurrence of the float64 Sturm count in range: when
+// |p| < 2^-623, p and its predecessor pp are both multiplied by 2^600 (the
+// signs, and so the count, are unchanged).  Done on the exponent fields with
+// integer operations, so that the FP64 pipe, the bottleneck of the
+// recurrence, issues nothing for it; pp's exponent saturates below the
+// infinity code (pp then dominates p by more than 2^1000, and the next minor
+// takes pp's sign either way).
+__device__ __forceinline__ void rescale_pair(double &p, double &pp) {
+    const int hp = __double2hiint(p), hq = __double2hiint(pp);
+    const int add = (((hp >> 20) & 0x7ff) < 400) ? 600 : 0;
+    const int eq = min(((hq >> 20) & 0x7ff) + add, 2046);
+    p = __hiloint2double(hp + (add << 20), __double2loint(p));
+    pp = __hiloint2double((hq & static_cast<int>(0x800fffffu)) | (eq << 20), __double2loint(pp));
+}
+
+// Steps 2-3 of cta_eigh_smallest: w[0..k) = eigenvalues of T / ||T|| to
+// 1e-10 (brackets' midpoints).  d, e: T (scaled in place to T / ||T||);
+// e2 (EIG_MAXM doubles), df, e2f (EIG_MAXM floats), iwk (512 ints) scratch.
+// Returns ||T||.
+__device__ double cta_tri_eigvals(int m, int k, double *d, double *e, double *e2, float *df, float *e2f, int *iwk,
+                                  double *w) {
+    __shared__ unsigned long long tnb[EIG_THREADS / 32];
+    __shared__ double blo[32], bhi[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // ||T||_inf: non-negative doubles compare as their bit patterns
+    unsigned long long tb = 0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        double t = fabs(d[r]);
+        if (r > 0) t += fabs(e[r - 1]);
+        if (r + 1 < m) t += fabs(e[r]);
+        tb = max(tb, static_cast<unsigned long long>(__double_as_longlong(t)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tb = max(tb, __shfl_xor_sync(0xffffffffu, tb, o));
+    if (lane == 0) tnb[warp] = tb;
+    __syncthreads();
+    tb = 0;
+    for (int q = 0; q < nwarps; ++q) tb = max(tb, tnb[q]);
+    double tnorm = __longlong_as_double(static_cast<long long>(tb));
+    if (!(tnorm > 0.0)) tnorm = 1.0;
     const double sc = rcp64(tnorm);
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
         const double ds = d[r] * sc;
@@ -472,73 +526,111 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
         }
     }
     __syncthreads();
-    // 2. float32 multisection: 32 points per step, each step narrows the
-    //    bracket 33-fold.  The float32 count is that of a matrix within a few
-    //    float32 roundings of T, so the bracket is widened by 4e-6.
-    for (int i = warp; i < k; i += nwarps) {
-        float flo = -1.f, fhi = 1.f;
-        for (int it = 0; it < 8 && fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f; ++it) {
-            const float x = flo + (fhi - flo) * static_cast<float>(lane + 1) / 33.f;
-            int cnt = 0;
-            float q = df[0] - x;
+    // float32 Sturm count at x (number of eigenvalues of T / ||T|| below x,
+    // up to float32 rounding of T)
+    auto count32 = [&](float x) {
+        int cnt = 0;
+        float q = df[0] - x;
+        cnt += q < 0.f;
+        for (int r = 1; r < m; ++r) {
+            if (fabsf(q) < 1e-30f) q = (q < 0.f) ? -1e-30f : 1e-30f;
+            q = (df[r] - x) - __fdividef(e2f[r - 1], q);
             cnt += q < 0.f;
-            for (int r = 1; r < m; ++r) {
-                if (fabsf(q) < 1e-30f) q = (q < 0.f) ? -1e-30f : 1e-30f;
-                q = (df[r] - x) - __fdividef(e2f[r - 1], q);
-                cnt += q < 0.f;
-            }
-            const unsigned above = __ballot_sync(0xffffffffu, cnt > i);
-            const int first = above ? (__ffs(above) - 1) : 32;    // first point with cnt > i
-            const float nlo = (first == 0) ? flo : flo + (fhi - flo) * static_cast<float>(first) / 33.f;
-            const float nhi = (first == 32) ? fhi : flo + (fhi - flo) * static_cast<float>(first + 1) / 33.f;
-            flo = nlo;
-            fhi = nhi;
         }
-        if (lane == 0) {
+        return cnt;
+    };
+    // 2a. counts at 256 points x_t = -1 + 2 (t + 1) / 257; for each i < k,
+    //     nb[warp][i] = points of this warp with count > i
+    int *nb = iwk;   // [nwarps][32]
+    {
+        const int c = count32(-1.f + 2.f * static_cast<float>(threadIdx.x + 1) / 257.f);
+        for (int i = 0; i < k; ++i) {
+            const unsigned above = __ballot_sync(0xffffffffu, c > i);
+            if (lane == 0) nb[warp * 32 + i] = __popc(above);
+        }
+    }
+    __syncthreads();
+    // 2b. first point with count > i is 256 - (points above): bracket
+    //     between it and its left neighbour; then G lanes per eigenvalue
+    //     narrow it (G + 1)-fold per step to 2e-7 relative
+    const int G = (k <= 8) ? 32 : (k <= 16 ? 16 : 8);
+    {
+        const int i = threadIdx.x / G, gl = threadIdx.x % G;
+        const bool act = i < k;
+        float flo = -1.f, fhi = 1.f;
+        if (act) {
+            int above = 0;
+            for (int q = 0; q < nwarps; ++q) above += nb[q * 32 + i];
+            const int first = 256 - above;   // first point with count > i (256: none)
+            flo = (first == 0) ? -1.f : -1.f + 2.f * static_cast<float>(first) / 257.f;
+            fhi = (first == 256) ? 1.f : -1.f + 2.f * static_cast<float>(first + 1) / 257.f;
+        }
+        const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        for (int it = 0; it < 6; ++it) {
+            const bool more = act && fhi - flo > 2e-7f * fmaxf(fabsf(flo), fabsf(fhi)) + 1e-30f;
+            if (!__any_sync(0xffffffffu, more)) break;
+            const float x = flo + (fhi - flo) * static_cast<float>(gl + 1) / static_cast<float>(G + 1);
+            const int c = act ? count32(x) : 0;
+            const unsigned ab = __ballot_sync(0xffffffffu, act && c > i) & gmask;
+            if (more) {
+                const unsigned grp = ab >> (lane & ~(G - 1));
+                const int first = grp ? (__ffs(grp) - 1) : G;
+                const float w0 = fhi - flo;
+                const float nlo = (first == 0) ? flo : flo + w0 * static_cast<float>(first) / static_cast<float>(G + 1);
+                const float nhi = (first == G) ? fhi : flo + w0 * static_cast<float>(first + 1) / static_cast<float>(G + 1);
+                flo = nlo;
+                fhi = nhi;
+            }
+        }
+        // the float32 count is that of a matrix within a few float32
+        // roundings of T: widen by 4e-6
+        if (act && gl == 0) {
             blo[i] = fmax(-1.0 - 1e-5, static_cast<double>(flo) - 4e-6);
             bhi[i] = fmin(1.0 + 1e-5, static_cast<double>(fhi) + 4e-6);
         }
     }
     __syncthreads();
-    // 3. float64 bisection, warps 0..3: eigenvalue i on lanes [i npts, (i+1) npts)
-    //    of the 128, npts a power of two (so a group lies within one warp)
+    // 3. float64 bisection on warps 0..3: gpw eigenvalues per warp, npts
+    //    points each (lanes [g npts, (g + 1) npts) of the warp)
     if (warp < 4) {
-        int npts = 32;
-        while (npts > 1 && npts * k > 128) npts >>= 1;
-        const int gl = warp * 32 + lane;
-        const int i = gl / npts, jp = gl % npts;
-        const bool act = i < k;
+        const int gpw = (k + 3) / 4;
+        const int npts = 32 / gpw;
+        const int g = lane / npts, jp = lane % npts;
+        const int i = warp * gpw + g;
+        const bool act = g < gpw && i < k;
         const double frac = static_cast<double>(jp + 1) / static_cast<double>(npts + 1);
         const double step = 1.0 / static_cast<double>(npts + 1);
+        const unsigned gmask = ((npts == 32) ? 0xffffffffu : ((1u << npts) - 1u)) << (g * npts);
         double lo = act ? blo[i] : 0.0, hi = act ? bhi[i] : 0.0;
         for (int it = 0; it < 40; ++it) {
             const bool done = !act || !(hi - lo > 1e-10);
             if (__all_sync(0xffffffffu, done)) break;
             const double x = fma(hi - lo, frac, lo);
             int cnt = 0;
-            if (act) {
-                // a zero minor takes the sign opposite to the previous one (it
-                // counts as a sign change, as a zero pivot counts as negative)
+            {
+                // a zero minor takes the sign opposite to the previous one
+                // (a sign change, as a zero pivot counts as negative): the
+                // bit pattern of -p 2^-80
                 double pp = 1.0, p = d[0] - x;
                 if ((__double_as_longlong(p) << 1) == 0) p = -0x1p-80;
                 cnt += __double2hiint(p) < 0;
+                rescale_pair(p, pp);
                 for (int r = 1; r < m; ++r) {
                     const double t = e2[r - 1] * pp;
                     double pn = fma(d[r] - x, p, -t);
-                    if ((__double_as_longlong(pn) << 1) == 0) pn = -p * 0x1p-80;
+                    if ((__double_as_longlong(pn) << 1) == 0)
+                        pn = __hiloint2double(static_cast<int>((static_cast<unsigned>(__double2hiint(p)) ^ 0x80000000u) -
+                                                               (80u << 20)),
+                                              __double2loint(p));
                     cnt += (__double2hiint(pn) ^ __double2hiint(p)) < 0;
                     pp = p;
                     p = pn;
-                    if (((__double2hiint(p) >> 20) & 0x7ff) < 400) {   // |p| < 2^-623: rescale both (rare)
-                        p *= 0x1p+600;
-                        pp *= 0x1p+600;
-                    }
+                    rescale_pair(p, pp);
                 }
             }
-            const unsigned above = __ballot_sync(0xffffffffu, act && cnt > i);
+            const unsigned above = __ballot_sync(0xffffffffu, act && cnt > i) & gmask;
             if (act && !done) {
-                const int sh = (i * npts) & 31;
-                const unsigned grp = (above >> sh) & ((npts == 32) ? 0xffffffffu : ((1u << npts) - 1u));
+                const unsigned grp = above >> (g * npts);
                 const int first = grp ? (__ffs(grp) - 1) : npts;   // first point with cnt > i
                 const double w0 = hi - lo;
                 const double nlo = (first == 0) ? lo : fma(w0, step * first, lo);
@@ -550,72 +642,128 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
         if (act && jp == 0) w[i] = 0.5 * (lo + hi);
     }
     __syncthreads();
-    // 4. inverse iteration (T scaled by 1 / ||T||): pair i on warp i % 4, lane i / 4
-    if (warp < 4 && lane < (k + 3) / 4 && lane * 4 + warp < k) {
-        const int i = lane * 4 + warp;
+    return tnorm;
+}
+
+// Row stride of the eigenvector block V (m x k) in shared memory: with
+// cpw columns per warp slot in the back-transformation, ldv = cpw (mod 16)
+// puts the 16 lanes of a half-warp on 16 different 8-byte banks; ldv = k if
+// that does not fit in the m x m region.
+__host__ __device__ inline int eig_ldv(int m, int k) {
+    const int ncw = (k + 3) / 4;
+    int cpw = 1;
+    while (cpw < ncw) cpw <<= 1;
+    int ldv = k;
+    while ((ldv - cpw) % 16 != 0) ++ldv;
+    return (ldv <= m) ? ldv : k;
+}
+
+__device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V, int ldv, double *d, double *e,
+                                  double *tau, double *y, double *wk) {
+    __shared__ double e2[EIG_MAXM];
+    __shared__ float df[EIG_MAXM], e2f[EIG_MAXM];
+    __shared__ double red_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // 1. tridiagonalisation (wk: x, v, w; y: A22 x)
+    cta_tridiag(A, m, d, e, tau, wk, y, wk + EIG_MAXM, wk + 2 * EIG_MAXM);
+    // 2-3. eigenvalues of T / ||T|| (d, e scaled in place)
+    const double tnorm = cta_tri_eigvals(m, k, d, e, e2, df, e2f, reinterpret_cast<int *>(wk), w);
+    // 4. inverse iteration on T / ||T||, pair i on lane i of warp 0: LU with
+    //    partial pivoting of T - w_i I carried in registers row by row (the
+    //    pivot row's reciprocal, multiplier and first and second
+    //    superdiagonals kept for the solves), then two solves from a fixed
+    //    start vector
+    if (warp == 0 && lane < k) {
+        const int i = lane;
         const double lam = w[i];
-        double D[EIG_MAXM], DL[EIG_MAXM], DU[EIG_MAXM], DU2[EIG_MAXM], rD[EIG_MAXM], y[EIG_MAXM];
-        bool piv[EIG_MAXM];
+        double rD[EIG_MAXM], DLf[EIG_MAXM], DUs[EIG_MAXM], DU2s[EIG_MAXM], yv[EIG_MAXM];
+        unsigned pivm[(EIG_MAXM + 31) / 32] = {};
         const double pert = 0x1p-52;   // replaces an exactly zero pivot (T scaled to norm 1)
-        for (int r = 0; r < m; ++r) {
-            D[r] = d[r] - lam;
-            DL[r] = (r + 1 < m) ? e[r] : 0.0;
-            DU[r] = DL[r];
-            DU2[r] = 0.0;
-        }
+        double Dc = d[0] - lam;
+        double Uc = (m > 1) ? e[0] : 0.0;
         for (int r = 0; r + 1 < m; ++r) {
-            const bool sw_ = !abs_ge(D[r], DL[r]);
-            piv[r] = sw_;
-            const double pvt = sw_ ? DL[r] : D[r];
-            const double rp = rcp64(pvt == 0.0 ? pert : pvt);
+            const double Lr = e[r];
+            const double Dn = d[r + 1] - lam;
+            const double Un = (r + 2 < m) ? e[r + 1] : 0.0;
+            const bool sw = !abs_ge(Dc, Lr);
+            double pvt = sw ? Lr : Dc;
+            if ((__double_as_longlong(pvt) << 1) == 0) pvt = pert;
+            const double rp = rcp64(pvt);
             rD[r] = rp;
-            if (!sw_) {
-                const double f = DL[r] * rp;
-                DL[r] = f;
-                D[r + 1] = fma(-f, DU[r], D[r + 1]);
-            } else {
-                const double f = D[r] * rp;
-                D[r] = pvt;
-                DL[r] = f;
-                const double t = DU[r];
-                DU[r] = D[r + 1];
-                D[r + 1] = fma(-f, D[r + 1], t);
-                if (r + 2 < m) {
-                    DU2[r] = DU[r + 1];
-                    DU[r + 1] = -f * DU[r + 1];
-                }
-            }
+            const double f = (sw ? Dc : Lr) * rp;
+            DLf[r] = f;
+            const double a = sw ? Dn : Uc;   // U[r][r+1]
+            const double b = sw ? Uc : Dn;
+            DUs[r] = a;
+            DU2s[r] = sw ? Un : 0.0;         // U[r][r+2]
+            Dc = fma(-f, a, b);
+            Uc = sw ? -f * Un : Un;
+            if (sw) pivm[r >> 5] |= 1u << (r & 31);
         }
-        rD[m - 1] = rcp64(D[m - 1] == 0.0 ? pert : D[m - 1]);
+        if ((__double_as_longlong(Dc) << 1) == 0) Dc = pert;
+        rD[m - 1] = rcp64(Dc);
         // start vector 1 + (small multiples of 1/44), exact in float32
-        for (int r = 0; r < m; ++r) y[r] = f64_exact(1.f + 0.25f * static_cast<float>((r * 7 + i * 13) % 11) / 11.f);
+        for (int r = 0; r < m; ++r) yv[r] = f64_exact(1.f + 0.25f * static_cast<float>((r * 7 + i * 13) % 11) / 11.f);
         for (int sweep = 0; sweep < 2; ++sweep) {
+            // L^{-1} with the row exchanges
+            double cur = yv[0];
             for (int r = 0; r + 1 < m; ++r) {
-                if (!piv[r]) {
-                    y[r + 1] = fma(-DL[r], y[r], y[r + 1]);
-                } else {
-                    const double t = y[r];
-                    y[r] = y[r + 1];
-                    y[r + 1] = fma(-DL[r], y[r], t);
+                const double nx = yv[r + 1];
+                const bool pv = (pivm[r >> 5] >> (r & 31)) & 1u;
+                const double a = pv ? nx : cur;
+                const double b = pv ? cur : nx;
+                yv[r] = a;
+                cur = fma(-DLf[r], a, b);
+            }
+            // U^{-1}, no normalisation between the two solves: each grows y
+            // by at most 1 / (smallest pivot) <= 2^52, far inside the range
+            double y1 = cur * rD[m - 1];
+            yv[m - 1] = y1;
+            if (m >= 2) {
+                double y2 = y1;
+                y1 = fma(-DUs[m - 2], y2, yv[m - 2]) * rD[m - 2];
+                yv[m - 2] = y1;
+                for (int r = m - 3; r >= 0; --r) {
+                    const double yr = fma(-DU2s[r], y2, fma(-DUs[r], y1, yv[r])) * rD[r];
+                    yv[r] = yr;
+                    y2 = y1;
+                    y1 = yr;
                 }
             }
-            y[m - 1] *= rD[m - 1];
-            if (m >= 2) y[m - 2] = fma(-DU[m - 2], y[m - 1], y[m - 2]) * rD[m - 2];
-            for (int r = m - 3; r >= 0; --r) y[r] = fma(-DU2[r], y[r + 2], fma(-DU[r], y[r + 1], y[r])) * rD[r];
-            // no normalisation between the two solves: each grows y by at
-            // most 1 / (smallest pivot) <= 2^52, far inside the float64 range
         }
-        double n0 = 0.0, n1 = 0.0, q0 = 0.0, q1 = 0.0;
-        for (int r = 0; r < m; ++r) {
-            double ty = d[r] * y[r];
-            if (r > 0) ty = fma(e[r - 1], y[r - 1], ty);
-            if (r + 1 < m) ty = fma(e[r], y[r + 1], ty);
-            if (r & 1) { n1 = fma(y[r], y[r], n1); q1 = fma(y[r], ty, q1); }
-            else { n0 = fma(y[r], y[r], n0); q0 = fma(y[r], ty, q0); }
+        for (int r = 0; r < m; ++r) V[r * ldv + i] = yv[r];
+    }
+    __syncthreads();
+    // norms and Rayleigh quotients y^T T y / y^T y: four pairs per warp,
+    // eight lanes per pair over rows r = rl + 8 t
+    {
+        const int g = lane >> 3, rl = lane & 7;
+        const int i = warp * 4 + g;
+        if (warp * 4 < k) {   // warp-uniform
+            const bool act = i < k;
+            double n0 = 0.0, q0 = 0.0;
+            if (act) {
+                for (int r = rl; r < m; r += 8) {
+                    const double yr = V[r * ldv + i];
+                    double ty = d[r] * yr;
+                    if (r > 0) ty = fma(e[r - 1], V[(r - 1) * ldv + i], ty);
+                    if (r + 1 < m) ty = fma(e[r], V[(r + 1) * ldv + i], ty);
+                    n0 = fma(yr, yr, n0);
+                    q0 = fma(yr, ty, q0);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+                q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+            }
+            __syncwarp();   // every lane of the pair has read V before it is scaled
+            if (act) {
+                const double rn = rsqrt64(n0);
+                if (rl == 0) w[i] = q0 * (rn * rn) * tnorm;
+                for (int r = rl; r < m; r += 8) V[r * ldv + i] *= rn;
+            }
         }
-        const double rn = rsqrt64(n0 + n1);
-        w[i] = (q0 + q1) * (rn * rn) * tnorm;   // Rayleigh quotient y^T T y / y^T y
-        for (int r = 0; r < m; ++r) V[r * k + i] = y[r] * rn;
     }
     __syncthreads();
     // re-orthogonalise vectors of (nearly) equal eigenvalues, in order
@@ -630,38 +778,48 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
                 if (fabs(w[i] - w[j2]) > 1e-10 * tnorm) continue;
                 if (threadIdx.x == 0) {
                     double dot = 0.0;
-                    for (int r = 0; r < m; ++r) dot += V[r * k + i] * V[r * k + j2];
+                    for (int r = 0; r < m; ++r) dot += V[r * ldv + i] * V[r * ldv + j2];
                     red_s = dot;
                 }
                 __syncthreads();
-                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] -= red_s * V[r * k + j2];
+                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * ldv + i] -= red_s * V[r * ldv + j2];
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     double nrm = 0.0;
-                    for (int r = 0; r < m; ++r) nrm += V[r * k + i] * V[r * k + i];
+                    for (int r = 0; r < m; ++r) nrm += V[r * ldv + i] * V[r * ldv + i];
                     red_s = 1.0 / sqrt(nrm);
                 }
                 __syncthreads();
-                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * k + i] *= red_s;
+                for (int r = threadIdx.x; r < m; r += blockDim.x) V[r * ldv + i] *= red_s;
                 __syncthreads();
             }
         }
     }
-    // 5. V = Q Y: reflectors H_j = I - tau_j v_j v_j^T, last first.  Warps
-    //    0..3 (one per sub-partition) own columns c = warp + 4 u; a warp's
-    //    lanes are cpw column slots x RG row groups (row r in group r % RG),
-    //    so one FP64 instruction serves cpw columns and the reflectors need no
-    //    barrier between them.
+    // 5. V = Q Y: reflectors H_j = I - tau_j v_j v_j^T, last first.  Warp
+    //    c4 < 4 owns columns [c4 ncw, (c4 + 1) ncw); its lanes are cpw column
+    //    slots x RG row groups (lane = rg cpw + cl), reflector j touching
+    //    rows j + 1 + rg + RG t; __syncwarp orders the lanes' shared updates
     if (warp < 4) {
-        const int ncol = (k - warp + 3) / 4;               // columns of this warp
+        const int ncw = (k + 3) / 4;
         int cpw = 1;
-        while (cpw < ncol) cpw <<= 1;                      // 1, 2, 4 or 8
-        const int RG = 32 / cpw;                           // row groups (>= 4)
-        const int rows = (m + RG - 1) / RG;                // rows per lane (<= 24)
-        if (rows <= 4) back_transform<4>(A, tau, V, m, k, warp, lane, RG, ncol);
-        else if (rows <= 8) back_transform<8>(A, tau, V, m, k, warp, lane, RG, ncol);
-        else if (rows <= 12) back_transform<12>(A, tau, V, m, k, warp, lane, RG, ncol);
-        else back_transform<24>(A, tau, V, m, k, warp, lane, RG, ncol);
+        while (cpw < ncw) cpw <<= 1;
+        const int RG = 32 / cpw;
+        const int cl = lane % cpw, rg = lane / cpw;
+        const int c = warp * ncw + cl;
+        const bool colok = cl < ncw && c < k;
+        for (int j = m - 3; j >= 0; --j) {
+            const double tj = tau[j];
+            if (tj == 0.0) continue;
+            const double *vr = A + j * m;
+            double dot = 0.0;
+            if (colok)
+                for (int r = j + 1 + rg; r < m; r += RG) dot = fma(vr[r], V[r * ldv + c], dot);
+            for (int o = cpw; o < 32; o <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            dot *= tj;
+            if (colok)
+                for (int r = j + 1 + rg; r < m; r += RG) V[r * ldv + c] = fma(-dot, vr[r], V[r * ldv + c]);
+            __syncwarp();
+        }
     }
     __syncthreads();
 }
@@ -682,9 +840,11 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
                                 double *Cout, double *theta, int *status) {
     extern __shared__ __align__(16) double sm[];
     double *sG = sm, *sO = sG + m * m, *sV = sO + m * m;
-    __shared__ double cs[2 * 64];
-    __shared__ int pairs[2 * 64];
-    __shared__ double wsort[96], sig[96];
+    // wk: Jacobi rotations and pairs, then the scaling of the eigen route,
+    // then the eigensolver's scratch
+    __shared__ double wk[3 * EIG_MAXM];
+    __shared__ double wsort[EIG_MAXM];
+    double *sig = wk + 144;
     __shared__ double tdd[EIG_MAXM], tee[EIG_MAXM], ttau[EIG_MAXM], tpv[EIG_MAXM];
     __shared__ int kept;
     __shared__ double red_big;
@@ -725,7 +885,7 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
         st = 3;
         mm = m;
         load(mm);
-        cta_jacobi(sO, sV, mm, cs, pairs, 30);         // O = U diag(s) U^T, U in sV
+        cta_jacobi(sO, sV, mm, wk, reinterpret_cast<int *>(wk + 96), 30);   // O = U diag(s) U^T, U in sV
         if (threadIdx.x == 0) {
             double smax = 0.0;
             for (int i = 0; i < mm; ++i) smax = fmax(smax, sO[i * mm + i]);
@@ -774,18 +934,19 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
     }
     __syncthreads();
     // k smallest eigenpairs of G_hat; eigenvectors (mm x k) into sV
-    cta_eigh_smallest(sG, mm, k, wsort, sV, tdd, tee, ttau, tpv);
+    const int ldv = eig_ldv(mm, k);
+    cta_eigh_smallest(sG, mm, k, wsort, sV, ldv, tdd, tee, ttau, tpv, wk);
     // C = L^{-T} Y (Cholesky route) or U s^{-1/2} Y (sO[p][i] = U[i][p]
     // s_p^{-1/2}); rows of a dropped P block are zero; undo the P scaling
-    if (chol) cta_trsm_rows_t(sO, rdv, sV, mm, k);
+    if (chol) cta_trsm_rows_t(sO, rdv, sV, mm, k, ldv);
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
         double sacc = 0.0;
         if (i < mm) {
             if (chol) {
-                sacc = sV[i * k + j];
+                sacc = sV[i * ldv + j];
             } else {
-                for (int p = 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * k + j];
+                for (int p = 0; p < mm; ++p) sacc += sO[p * mm + i] * sV[p * ldv + j];
             }
             if (pscale && i >= p0) sacc *= pscale[i - p0];
         }
