@@ -76,6 +76,28 @@ __device__ __forceinline__ double rsqrt64(double s) {
     r = r * fma(-hs, r * r, 1.5);
     return r * fma(-hs, r * r, 1.5);
 }
+// Third-order (Householder) refinements of the same float32 estimates: one
+// step takes the ~2^-22 relative error of the estimate to ~2^-64, with a
+// dependent chain of 3 (reciprocal) or 4 (reciprocal square root) FP64
+// operations instead of 4 or 6.
+//   1/q:       e = 1 - q r,     r' = r (1 + e + e^2)
+//   1/sqrt(s): e = 1 - s r^2,   r' = r (1 + e/2 + 3 e^2/8)
+__device__ __forceinline__ double rcp64c(double q) {
+    if (!in_seed_range(q)) return 1.0 / q;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(q)));
+    const double r = f64_exact(rf);
+    const double e = fma(-q, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+__device__ __forceinline__ double rsqrt64c(double s) {
+    if (!in_seed_range(s)) return 1.0 / sqrt(s);
+    float rf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(s)));
+    const double r = f64_exact(rf);
+    const double e = fma(-s * r, r, 1.0);
+    return fma(r * e, fma(e, 0.375, 0.5), r);
+}
 // |a| >= |b| on the bit patterns (integer compare, no FP64 instruction).
 __device__ __forceinline__ bool abs_ge(double a, double b) {
     return (static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7fffffffffffffffull) >=
@@ -151,40 +173,6 @@ __device__ void cta_tri_inverse(const double *L, const double *rd, double *Li, i
             Li[i * m + j] = s * rd[i];
         }
     }
-    __syncthreads();
-}
-
-// B <- L^{-1} B for lower-triangular L (m x m) with rd[i] = 1 / L_ii; B is
-// m x nc, row stride nc (nc <= blockDim).  Right-looking: at step i row i
-// holds L_ii z_i (z = L^{-1} B), and rows below subtract L[r][i] z_i.  Rows
-// are scaled by rd at the end.  One barrier per step.
-__device__ void cta_trsm_rows(const double *L, const double *rd, double *B, int m, int nc) {
-    const int per = blockDim.x / nc;                 // rows per pass
-    const int c = threadIdx.x % nc, r0 = threadIdx.x / nc;
-    for (int i = 0; i + 1 < m; ++i) {
-        if (r0 < per) {
-            const double zi = B[i * nc + c] * rd[i];
-            for (int r = i + 1 + r0; r < m; r += per) B[r * nc + c] = fma(-L[r * m + i], zi, B[r * nc + c]);
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) B[e] *= rd[e / nc];
-    __syncthreads();
-}
-
-// Y <- L^{-T} Y (Y m x nc, row stride ldy): back substitution, right-looking
-// from the last row, same conventions as cta_trsm_rows.
-__device__ void cta_trsm_rows_t(const double *L, const double *rd, double *Y, int m, int nc, int ldy) {
-    const int per = blockDim.x / nc;
-    const int c = threadIdx.x % nc, r0 = threadIdx.x / nc;
-    for (int i = m - 1; i > 0; --i) {
-        if (r0 < per) {
-            const double ci = Y[i * ldy + c] * rd[i];
-            for (int r = r0; r < i; r += per) Y[r * ldy + c] = fma(-L[i * m + r], ci, Y[r * ldy + c]);
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) Y[(e / nc) * ldy + e % nc] *= rd[e / nc];
     __syncthreads();
 }
 
@@ -365,11 +353,11 @@ __device__ void cta_tridiag(double *A, int m, double *d, double *e, double *tau,
                     e[j] = x0;
                 } else {
                     const double s2 = fma(x0, x0, sg);
-                    const double r = rsqrt64(s2);
+                    const double r = rsqrt64c(s2);
                     const double mu = s2 * r;
                     const double alpha = (x0 <= 0.0) ? mu : -mu;
                     scal[0] = fma(fabs(x0), r, 1.0);
-                    scal[1] = rcp64(x0 - alpha);
+                    scal[1] = rcp64c(x0 - alpha);
                     scal[2] = alpha;
                     e[j] = alpha;
                 }
@@ -513,7 +501,7 @@ __device__ double cta_tri_eigvals(int m, int k, double *d, double *e, double *e2
     for (int q = 0; q < nwarps; ++q) tb = max(tb, tnb[q]);
     double tnorm = __longlong_as_double(static_cast<long long>(tb));
     if (!(tnorm > 0.0)) tnorm = 1.0;
-    const double sc = rcp64(tnorm);
+    const double sc = rcp64c(tnorm);
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
         const double ds = d[r] * sc;
         d[r] = ds;
@@ -688,7 +676,7 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             const bool sw = !abs_ge(Dc, Lr);
             double pvt = sw ? Lr : Dc;
             if ((__double_as_longlong(pvt) << 1) == 0) pvt = pert;
-            const double rp = rcp64(pvt);
+            const double rp = rcp64c(pvt);
             rD[r] = rp;
             const double f = (sw ? Dc : Lr) * rp;
             DLf[r] = f;
@@ -701,7 +689,7 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             if (sw) pivm[r >> 5] |= 1u << (r & 31);
         }
         if ((__double_as_longlong(Dc) << 1) == 0) Dc = pert;
-        rD[m - 1] = rcp64(Dc);
+        rD[m - 1] = rcp64c(Dc);
         // start vector 1 + (small multiples of 1/44), exact in float32
         for (int r = 0; r < m; ++r) yv[r] = f64_exact(1.f + 0.25f * static_cast<float>((r * 7 + i * 13) % 11) / 11.f);
         for (int sweep = 0; sweep < 2; ++sweep) {
@@ -759,7 +747,7 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
             }
             __syncwarp();   // every lane of the pair has read V before it is scaled
             if (act) {
-                const double rn = rsqrt64(n0);
+                const double rn = rsqrt64c(n0);
                 if (rl == 0) w[i] = q0 * (rn * rn) * tnorm;
                 for (int r = rl; r < m; r += 8) V[r * ldv + i] *= rn;
             }
@@ -824,6 +812,171 @@ __device__ void cta_eigh_smallest(double *A, int m, int k, double *w, double *V,
     __syncthreads();
 }
 
+// Cholesky O = L L^T for the Rayleigh-Ritz solve (A: m x m in shared
+// memory, lower triangle read).  One barrier per column: warp 0 finishes
+// column j + 1 (its update by column j, pivot, scaling) while the other warps
+// apply column j to the rest of the trailing triangle; L's columns are kept
+// as rows of the upper triangle so that those updates read contiguous rows.
+// On success: rd[j] = 1 / L_jj, A[j][j] = L_jj and, for r < i,
+//   A[i][r] = L_ir / L_ii   (lower, rows scaled: the back substitution)
+//   A[r][i] = L_ir / L_rr   (upper, columns scaled: the forward substitution)
+// Returns false if a pivot is not > 0 or the pivots span more than `span`
+// (max L_jj / min L_jj); A is then not usable.
+__device__ bool cta_cholesky_rr(double *A, int m, double span, double *rd) {
+    __shared__ int ok;
+    __shared__ double sp_min, sp_max;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    double dmin = 1e300, dmax = 0.0;   // kept by warp 0
+    // pivot of column c (its entries below the diagonal final), then L's
+    // column c (unscaled) into row c of the upper triangle; warp 0
+    auto pivot = [&](int c) {
+        const double s = A[c * m + c];
+        if (!(s > 0.0)) {
+            if (lane == 0) ok = 0;
+            return;
+        }
+        const double r = rsqrt64c(s);
+        const double l = s * r;
+        dmin = fmin(dmin, l);
+        dmax = fmax(dmax, l);
+        if (lane == 0) {
+            A[c * m + c] = l;
+            rd[c] = r;
+        }
+        for (int i = c + 1 + lane; i < m; i += 32) A[c * m + i] = A[i * m + c] * r;
+    };
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    if (warp == 0) pivot(0);
+    __syncthreads();
+    for (int j = 0; j + 1 < m; ++j) {
+        if (!ok) break;
+        const double *Lj = A + j * m;   // Lj[i] = L_ij, i > j
+        if (warp == 0) {
+            const double ljp = Lj[j + 1];
+            for (int i = j + 1 + lane; i < m; i += 32) A[i * m + j + 1] = fma(-Lj[i], ljp, A[i * m + j + 1]);
+            __syncwarp();
+            pivot(j + 1);
+        } else {
+            const int n = m - j - 2;   // rows and columns j + 2 .. m - 1
+            const int tot = ((n + 1) >> 1) * (n + 1);
+            for (int q = threadIdx.x - 32; q < tot; q += blockDim.x - 32) {
+                int a, b;
+                if (!tri_fold(q, n, a, b)) continue;
+                const int i = j + 2 + a, l = j + 2 + b;
+                A[i * m + l] = fma(-Lj[i], Lj[l], A[i * m + l]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sp_min = dmin;
+        sp_max = dmax;
+    }
+    __syncthreads();
+    if (!ok) return false;
+    for (int i = warp; i < m; i += nwarps)
+        for (int r = lane; r < i; r += 32) {
+            const double lv = A[r * m + i];
+            A[i * m + r] = lv * rd[i];
+            A[r * m + i] = lv * rd[r];
+        }
+    __syncthreads();
+    return sp_max <= span * sp_min;
+}
+
+// B <- L^{-1} B (B: m x nc, row-major, shared) with L from cta_cholesky_rr
+// (A's upper triangle: A[i][r] = L_ri / L_ii).  Right-looking: at step i row
+// i holds L_ii z_i and rows r > i subtract A[i][r] times it; the rows are
+// scaled by 1 / L_rr at the end.  One barrier per step.
+__device__ void cta_trsm_fwd_rr(const double *A, const double *rd, double *B, int m, int nc) {
+    const int T = blockDim.x, dq = T / nc, dc = T % nc;
+    const int q0 = threadIdx.x / nc, c0 = threadIdx.x % nc;
+    for (int i = 0; i + 1 < m; ++i) {
+        const double *Lt = A + i * m;
+        const double *Bi = B + i * nc;
+        int r = i + 1 + q0, c = c0;
+        while (r < m) {
+            B[r * nc + c] = fma(-Lt[r], Bi[c], B[r * nc + c]);
+            r += dq;
+            c += dc;
+            if (c >= nc) {
+                c -= nc;
+                ++r;
+            }
+        }
+        __syncthreads();
+    }
+    int r = q0, c = c0;
+    while (r < m) {
+        B[r * nc + c] *= rd[r];
+        r += dq;
+        c += dc;
+        if (c >= nc) {
+            c -= nc;
+            ++r;
+        }
+    }
+    __syncthreads();
+}
+
+// G_hat = L^{-1} G L^{-T} from B = L^{-1} G (m x m, in place): column c of
+// G_hat solves L z = (row c of B)^T, and only z_0..z_c are formed (each
+// needs only the rows above it), in row c.  On return B's lower triangle
+// (diagonal included) is G_hat's; its upper triangle is not.
+__device__ void cta_trsm_sym_rr(const double *A, const double *rd, double *B, int m) {
+    for (int i = 0; i + 1 < m; ++i) {
+        const double *Lt = A + i * m;
+        const int n = m - 1 - i;   // rows c and columns r in i + 1 .. m - 1, r <= c
+        const int tot = ((n + 1) >> 1) * (n + 1);
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            int a, b;
+            if (!tri_fold(q, n, a, b)) continue;
+            const int c = i + 1 + a, r = i + 1 + b;
+            B[c * m + r] = fma(-Lt[r], B[c * m + i], B[c * m + r]);
+        }
+        __syncthreads();
+    }
+    const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < m; c += nwarps)
+        for (int r = lane; r <= c; r += 32) B[c * m + r] *= rd[r];
+    __syncthreads();
+}
+
+// Y <- L^{-T} Y (Y: m x nc, row stride ldy) with L from cta_cholesky_rr
+// (A's lower triangle: A[i][r] = L_ir / L_ii): back substitution from the
+// last row, rows scaled by 1 / L_rr at the end.
+__device__ void cta_trsm_bwd_rr(const double *A, const double *rd, double *Y, int m, int nc, int ldy) {
+    const int T = blockDim.x, dq = T / nc, dc = T % nc;
+    const int q0 = threadIdx.x / nc, c0 = threadIdx.x % nc;
+    for (int i = m - 1; i > 0; --i) {
+        const double *Li = A + i * m;
+        const double *Yi = Y + i * ldy;
+        int r = q0, c = c0;
+        while (r < i) {
+            Y[r * ldy + c] = fma(-Li[r], Yi[c], Y[r * ldy + c]);
+            r += dq;
+            c += dc;
+            if (c >= nc) {
+                c -= nc;
+                ++r;
+            }
+        }
+        __syncthreads();
+    }
+    int r = q0, c = c0;
+    while (r < m) {
+        Y[r * ldy + c] *= rd[r];
+        r += dq;
+        c += dc;
+        if (c >= nc) {
+            c -= nc;
+            ++r;
+        }
+    }
+    __syncthreads();
+}
+
 // Rayleigh-Ritz on the pencil (G, O) of eq. rreig: keep the k leftmost pairs.
 // G, O: m x m FP64 (global).  pscale (may be null): scale of the last m - p0
 // rows/columns (the P block), applied as D G D, D O D and undone in C.
@@ -864,22 +1017,18 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
         __syncthreads();
     };
     load(mm);
-    chol = cta_cholesky(sO, mm, 1e4, rdv);
+    chol = cta_cholesky_rr(sO, mm, 1e4, rdv);
     if (!chol && p0 < m) {
         mm = p0;
         st = 1;
         load(mm);
-        chol = cta_cholesky(sO, mm, 1e4, rdv);
+        chol = cta_cholesky_rr(sO, mm, 1e4, rdv);
     }
     if (chol) {
-        // G_hat = L^{-1} G L^{-T} = L^{-1} (L^{-1} G)^T (G symmetric): two
-        // forward substitutions with a transpose between them; L stays in sO
-        cta_trsm_rows(sO, rdv, sG, mm, mm);           // sG = L^{-1} G
-        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sV[(e % mm) * mm + e / mm] = sG[e];
-        __syncthreads();
-        cta_trsm_rows(sO, rdv, sV, mm, mm);           // sV = L^{-1} G L^{-T}
-        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) sG[e] = sV[e];
-        __syncthreads();
+        // G_hat = L^{-1} G L^{-T} = L^{-1} (L^{-1} G)^T (G symmetric): a
+        // forward substitution, then the lower triangle of the second one
+        cta_trsm_fwd_rr(sO, rdv, sG, mm, mm);         // sG = L^{-1} G
+        cta_trsm_sym_rr(sO, rdv, sG, mm);             // lower triangle of sG = G_hat
     } else {
         // eigen route on the full pencil
         st = 3;
@@ -924,21 +1073,23 @@ __global__ void k_rayleigh_ritz(int m, int k, int p0, const double *G, const dou
             return;
         }
     }
-    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-        const int i = e / mm, j = e % mm;
-        if (j > i) {
-            const double sv = 0.5 * (sG[i * mm + j] + sG[j * mm + i]);
-            sG[i * mm + j] = sv;
-            sG[j * mm + i] = sv;
+    if (!chol) {   // U^T G U from two products: symmetrise
+        for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+            const int i = e / mm, j = e % mm;
+            if (j > i) {
+                const double sv = 0.5 * (sG[i * mm + j] + sG[j * mm + i]);
+                sG[i * mm + j] = sv;
+                sG[j * mm + i] = sv;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     // k smallest eigenpairs of G_hat; eigenvectors (mm x k) into sV
     const int ldv = eig_ldv(mm, k);
     cta_eigh_smallest(sG, mm, k, wsort, sV, ldv, tdd, tee, ttau, tpv, wk);
     // C = L^{-T} Y (Cholesky route) or U s^{-1/2} Y (sO[p][i] = U[i][p]
     // s_p^{-1/2}); rows of a dropped P block are zero; undo the P scaling
-    if (chol) cta_trsm_rows_t(sO, rdv, sV, mm, k, ldv);
+    if (chol) cta_trsm_bwd_rr(sO, rdv, sV, mm, k, ldv);
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
         double sacc = 0.0;
