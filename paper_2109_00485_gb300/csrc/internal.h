@@ -54,6 +54,18 @@ struct Tiled {
     float *diag = nullptr;   // d_i = h_ii (float32)
 };
 
+// Float64-vector SpMM (spmm_df.cu): the off-diagonal chunks listed by
+// column tile (col_list[col_ptr[ct] .. col_ptr[ct + 1]): (chunk, row block),
+// in row-block order), built on first use; x_hi, x_lo of the last call
+// (x_lo at xs + xs_stride), allocated for up to xs_k columns.
+struct DfIndex {
+    int64_t *col_ptr = nullptr;
+    int2 *col_list = nullptr;
+    float *xs = nullptr;
+    int xs_k = 0;
+    int64_t xs_stride = 0;
+};
+
 // Diagonal tiles of the FOM preconditioner (fom.cu).  Small tiles (<= 64
 // rows): dense FP32 64 x 64 blocks, both triangles, zero outside the m x m
 // corner, one per small tile in s_t0 order.  Large tiles (> 64 rows), in
@@ -103,6 +115,7 @@ struct lobpcg_ctx {
     float *bj_Q = nullptr;       // block-Jacobi: per 64-row tile eigenvectors (64 x 64) and eigenvalues
     float *bj_lam = nullptr;
     lobpcg::FomTiles fom;        // FOM preconditioner tiles (fom.cu)
+    lobpcg::DfIndex df;          // float64-vector SpMM (spmm_df.cu)
     lobpcg::SolverState *solver = nullptr;  // workspaces of lobpcg_solve (solver.cu)
     lobpcg::DavState *dav = nullptr;        // workspaces of lobpcg_davidson (solver.cu), made on first use
     lobpcg::Mlp mlp;                         // learned tile preconditioner (mlp.cu)
@@ -137,7 +150,10 @@ cudaError_t build_tiled(lobpcg_ctx *h, const int64_t *row_ptr, const int32_t *co
 
 // spmm_sym.cu
 cudaError_t launch_spmm_sym_f32(const lobpcg_ctx *h, const float *X, float *Y, int k, cudaStream_t s);
-cudaError_t launch_spmm_sym_f64(const lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s);
+cudaError_t launch_spmm_sym_f64(lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s);
+// spmm_df.cu: the float64-vector product in compensated float32 (even k <= 32)
+bool spmm_df_ok(int k, const double *X, const double *Y);
+cudaError_t launch_spmm_sym_df(lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s);
 
 // helpers in api.cu
 cudaError_t dev_alloc(lobpcg_ctx *h, void **p, size_t bytes);

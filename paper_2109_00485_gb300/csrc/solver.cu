@@ -747,14 +747,7 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         CK(timed_spmm<float>(h, s, f.W, f.HW, k));
         const int na = hasP ? 3 : 2;
         const int m = na * k;
-        GemmBlocks<float> aS{}, aHS{}, aB{};
-        aS.p[0] = f.X; aS.p[1] = f.W; aS.p[2] = f.P;
-        aHS.p[0] = f.HX; aHS.p[1] = f.HW; aHS.p[2] = f.HP;
-        for (int q = 0; q < na; ++q) {
-            aB.p[q] = aHS.p[q];
-            aB.p[na + q] = aS.p[q];
-        }
-        CK(launch_gram<float>(n, k, na, aS, 2 * na, aB, s->G, h->num_sms, h->stream, h->d_err));
+        CK(gram_post<float>(h, s, f, na));   // [S^T HS | S^T S]; the X blocks are patched below
         GemmBlocks<double> ax{}, axx{};
         ax.p[0] = d.X;
         axx.p[0] = d.HX;

@@ -639,7 +639,8 @@ cudaError_t launch_spmm_sym_f32(const lobpcg_ctx *h, const float *X, float *Y, i
     return launch_simple<float>(h, X, Y, k, s);
 }
 
-cudaError_t launch_spmm_sym_f64(const lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s) {
+cudaError_t launch_spmm_sym_f64(lobpcg_ctx *h, const double *X, double *Y, int k, cudaStream_t s) {
+    if (spmm_df_ok(k, X, Y)) return launch_spmm_sym_df(h, X, Y, k, s);   // writes every row of Y
     cudaError_t e = cudaMemsetAsync(Y, 0, sizeof(double) * static_cast<size_t>(h->T.n) * k, s);
     if (e != cudaSuccess) return e;
     return launch_simple<double>(h, X, Y, k, s);
