@@ -71,6 +71,14 @@ cudaError_t launch_gram_pairs(int64_t n, int k, int nblk, const float *const *bl
 // S, HS: na (2 or 3) float32 n x k blocks, 16-byte aligned; k in {8, 16, 20}.
 // update.cu: Z = [A_0 .. A_{na-1}] C (one float32 output, in place allowed),
 // C (na k) x k FP64; k in {8, 16, 20}, na <= 3, 16-byte aligned blocks.
+// The float64 refinement's dense steps in compensated float32 (mixed_df.cu,
+// k <= 32): Z <- Z C + A with Z32 = float32(Z), as launch_xupdate; and
+// G = X^T [HX X] (k x 2k, zeroed first) from float64 X and HX.
+bool mixed_df_ok(int k);
+cudaError_t launch_xupdate_df(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_gram_x_df(int64_t n, int k, const double *X, const double *HX, double *G, int num_sms,
+                             cudaStream_t s);
 bool combine_ff_ok(int k, int na, const float *const *blocks, const float *Z);
 cudaError_t launch_combine_ff(int64_t n, int k, int na, const float *const *A, const double *C, float *Z, int *err,
                               int num_sms, cudaStream_t s);

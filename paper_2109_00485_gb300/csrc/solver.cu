@@ -748,11 +748,15 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         const int na = hasP ? 3 : 2;
         const int m = na * k;
         CK(gram_post<float>(h, s, f, na));   // [S^T HS | S^T S]; the X blocks are patched below
-        GemmBlocks<double> ax{}, axx{};
-        ax.p[0] = d.X;
-        axx.p[0] = d.HX;
-        axx.p[1] = d.X;
-        CK(launch_gram<double>(n, k, 1, ax, 2, axx, s->Gx, h->num_sms, h->stream, h->d_err));
+        if (mixed_df_ok(k)) {
+            CK(launch_gram_x_df(n, k, d.X, d.HX, s->Gx, h->num_sms, h->stream));   // [X^T HX | X^T X]
+        } else {
+            GemmBlocks<double> ax{}, axx{};
+            ax.p[0] = d.X;
+            axx.p[0] = d.HX;
+            axx.p[1] = d.X;
+            CK(launch_gram<double>(n, k, 1, ax, 2, axx, s->Gx, h->num_sms, h->stream, h->d_err));
+        }
         GemmBlocks<float> ar{}, awp{};
         ar.p[0] = R32;
         awp.p[0] = f.W;
@@ -778,8 +782,13 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         ohp.z[0] = f.HP; ohp.C[0] = s->C + static_cast<int64_t>(k) * k; ohp.c0[0] = 0; ohp.norm_of = -1;
         CK(launch_combine<float>(n, k, na - 1, aWP, 1, op, s->colsqP, h->num_sms, h->stream));
         CK(launch_combine<float>(n, k, na - 1, aHWP, 1, ohp, nullptr, h->num_sms, h->stream));
-        CK(launch_xupdate(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
-        CK(launch_xupdate(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
+        if (mixed_df_ok(k)) {
+            CK(launch_xupdate_df(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
+            CK(launch_xupdate_df(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
+        } else {
+            CK(launch_xupdate(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
+            CK(launch_xupdate(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
+        }
         hasP = true;
     }
     res.rho = rho;
