@@ -21,6 +21,8 @@ value_only_tiles: the SpMM and the diagonal solve with tile_format 1
              (complete tiles keep value words only), with GB/s on its own
              stream bytes -- reported beside the CSR-equivalent metric,
              never folded into it.
+spmm_f64   : lobpcg_spmm_sym_f64 (float64 X and Y, products in compensated
+             float32) on the same matrix, median of 5 launches.
 
 --impl reference times the CPU oracle (the only reference there is: the
 paper's code is not available) on the same metric.
@@ -340,6 +342,34 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
     return out
 
 
+def spmm_f64_report(pkg, A, p, stream, csr_bytes: int) -> dict:
+    """The float64-vector SpMM (lobpcg_spmm_sym_f64: the refinement's
+    explicit products, in compensated float32) on the same matrix: median
+    of 5 launches, CUDA events, X seeded N(0, 1) in float64."""
+    import torch
+    n, k = A.n, p["k"]
+    h = pkg.from_csr(A, k=k, nev=p["nev"], stream=stream)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(p["seed"])
+    with torch.cuda.stream(stream):
+        X = torch.randn(n, k, device="cuda", dtype=torch.float64, generator=g)
+        Y = torch.empty_like(X)
+    for _ in range(2):
+        h.spmm_sym_f64(X, Y)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for i in range(5):
+        evs[i].record(stream)
+        h.spmm_sym_f64(X, Y)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(evs[i].elapsed_time(evs[i + 1]) for i in range(5))
+    h.destroy()
+    # the float32 metric's bytes with X and Y in float64
+    own = csr_bytes + 2 * n * k * 4
+    return {"kernels": "k_split64, k_spmm_df_rows, k_spmm_df_cols (compensated float32)", "ms": round(ms, 3),
+            "gbs_csr_equivalent_f64_vectors": round(own / (ms / 1e3) / 1e9, 1)}
+
+
 def mlp_kernels_report(pkg, stream, peak_tflops: float, rows: int = 500_000, batch: int = 4096) -> dict:
     """The learned preconditioner's network kernels, timed with CUDA events
     against the measured dense bf16 peak: the forward pass (129 -> 256 -> 64,
@@ -524,6 +554,7 @@ def main():
     ap.add_argument("--no-largest", action="store_true", help="skip the n = 8M sub-record")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-value-only", action="store_true")
+    ap.add_argument("--no-f64", action="store_true", help="skip the float64-vector SpMM sub-record")
     ap.add_argument("--fom-only", action="store_true",
                     help="only the FOM preconditioner report (fom_apply) on the workload; for profiling")
     args = ap.parse_args()
@@ -626,6 +657,9 @@ def main():
     mlpk = None
     if rank == 0 and not args.no_solves:
         mlpk = mlp_kernels_report(pkg, stream, peaks["bf16_tflops"])
+    f64 = None
+    if rank == 0 and not args.no_f64:
+        f64 = spmm_f64_report(pkg, A, p, stream, B)
     largest = None
     if rank == 0 and not args.no_largest and not args.no_solves and args.workload == WORKLOAD:
         del A   # the n = 2M matrix's pinned host copy
@@ -649,6 +683,7 @@ def main():
                 "fom_apply": fom,
                 "value_only_tiles": vonly,
                 "mlp_kernels": mlpk,
+                "spmm_f64": f64,
                 "largest": largest,
                 "layout": {"chunks": info["chunks"], "full_chunks": info["full_chunks"],
                            "padded_nnz": info["padded_nnz"], "warps": info["warps"]}}
