@@ -72,13 +72,18 @@ cudaError_t launch_gram_pairs(int64_t n, int k, int nblk, const float *const *bl
 // update.cu: Z = [A_0 .. A_{na-1}] C (one float32 output, in place allowed),
 // C (na k) x k FP64; k in {8, 16, 20}, na <= 3, 16-byte aligned blocks.
 // The float64 refinement's dense steps in compensated float32 (mixed_df.cu,
-// k <= 32): Z <- Z C + A with Z32 = float32(Z), as launch_xupdate; and
-// G = X^T [HX X] (k x 2k, zeroed first) from float64 X and HX.
+// k <= 32): G = X^T [HX X] (k x 2k, zeroed first) from float64 X and HX,
+// and the fused update below.
 bool mixed_df_ok(int k);
-cudaError_t launch_xupdate_df(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
-                              cudaStream_t s);
 cudaError_t launch_gram_x_df(int64_t n, int k, const double *X, const double *HX, double *G, int num_sms,
                              cudaStream_t s);
+// Both updates and the next residual in one pass (mixed_df.cu): X <- X C + P,
+// HX <- HX C + HP (float64; X32, HX32 float32 copies), then R32 = HX - X
+// Theta, W = R32 (mode 0) or the diagonal-preconditioned R32 (mode 1), and
+// norms (zeroed first) = (||r_j||^2, ||x_j||^2), as launch_resid_mixed.
+cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, const float *P,
+                               const float *HP, float *X32, float *HX32, const double *theta, const float *d,
+                               float *W, float *R32, int mode, double *norms, int num_sms, cudaStream_t s);
 bool combine_ff_ok(int k, int na, const float *const *blocks, const float *Z);
 cudaError_t launch_combine_ff(int64_t n, int k, int na, const float *const *A, const double *C, float *Z, int *err,
                               int num_sms, cudaStream_t s);

@@ -1,8 +1,10 @@
 // Dense steps of the float64 refinement in compensated float32 (df.cuh):
 //
-//   k_xupdate_df   Z <- Z C + A (Z n x k float64 in place, C k x k float64,
-//                  A n x k float32) and Z32 = float32(Z): the X and HX
-//                  updates of the refinement
+//   k_xupdate2_df  X <- X C + P and HX <- HX C + HP (float64 in place, C
+//                  k x k float64, P and HP float32) with their float32
+//                  copies, and the next residual HX - X Theta, its
+//                  preconditioned copy and norms: the X and HX updates of
+//                  the refinement fused with the following residual
 //   k_gram_x_df    G = X^T [HX X] (k x 2k float64) from float64 X and HX:
 //                  the Gram blocks the refinement keeps in float64
 //
@@ -23,53 +25,130 @@ namespace {
 
 constexpr int XU_THREADS = 256;
 
-// thread (row r of the pass, column j); C split once per CTA, the pass's
-// rows of Z split once into shared memory
-__global__ void __launch_bounds__(XU_THREADS) k_xupdate_df(int64_t n, int k, double *Z, const double *C,
-                                                           const float *A, float *Z32) {
-    extern __shared__ float xs[];   // ch, cl (k x k each), zh, zl (per x k each)
+// Both updates and the next residual in one pass (k <= 32):
+//   X <- X C + P, HX <- HX C + HP (float64, X32 / HX32 their float32 copies)
+//   R = HX - X Theta (float32 R32), W = R (mode 0) or R / g(d_i - theta_j)
+//   (mode 1, the guarded diagonal preconditioner), norms += (||r_j||^2,
+//   ||x_j||^2).  The updated X and HX enter the residual as float pairs, so
+//   HX - X Theta is formed without cancellation loss: TwoSum of hx_hi and
+//   -fl(x_hi theta_hi), the rest in the low word.
+__global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C,
+                                                            const float *P, const float *HP, float *X32, float *HX32,
+                                                            const double *theta, const float *d, float *W, float *R32,
+                                                            int mode, double *norms) {
+    extern __shared__ float xs[];   // ch, cl (k x k), xh, xl, hh, hl (per x k each)
+    __shared__ double red[64];      // [2k]
     const int per = XU_THREADS / k;
-    float *ch = xs, *cl = xs + k * k, *zh = xs + 2 * k * k, *zl = zh + per * k;
+    float *ch = xs, *cl = xs + k * k, *xh = xs + 2 * k * k, *xl = xh + per * k, *hh = xl + per * k,
+          *hl = hh + per * k;
     for (int q = threadIdx.x; q < k * k; q += blockDim.x) df_split(C[q], ch[q], cl[q]);
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) red[q] = 0.0;
     const int r = threadIdx.x / k, j = threadIdx.x % k;
     const bool active = r < per;
+    float th_h = 0.f, th_l = 0.f;
+    if (active) df_split(theta[j], th_h, th_l);
+    const float thf = __fadd_rn(th_h, th_l);
+    const float delta = 1e-3f * fmaxf(1.f, fabsf(thf));
+    // float32 sums of nonnegative terms over this thread's rows (a few
+    // hundred at most: relative error below 1e-4, enough for the norms'
+    // use in the convergence test), folded into float64 once at the end
+    float rr = 0.f, xx = 0.f;
     for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * per; i0 < n; i0 += static_cast<int64_t>(gridDim.x) * per) {
         const int rows = static_cast<int>(n - i0 < per ? n - i0 : per);
         __syncthreads();
-        if (threadIdx.x < rows * k) df_split(Z[i0 * k + threadIdx.x], zh[threadIdx.x], zl[threadIdx.x]);
+        if (threadIdx.x < rows * k) {
+            df_split(X[i0 * k + threadIdx.x], xh[threadIdx.x], xl[threadIdx.x]);
+            df_split(HX[i0 * k + threadIdx.x], hh[threadIdx.x], hl[threadIdx.x]);
+        }
         __syncthreads();
         if (active && r < rows) {
-            float s = 0.f, c = 0.f;
-            for (int l = 0; l < k; ++l) df_mac(zh[r * k + l], zl[r * k + l], ch[l * k + j], cl[l * k + j], s, c);
+            float sx = 0.f, cx = 0.f, sh = 0.f, chh = 0.f;
+            for (int l = 0; l < k; ++l) {
+                const float a = ch[l * k + j], b = cl[l * k + j];
+                df_mac(xh[r * k + l], xl[r * k + l], a, b, sx, cx);
+                df_mac(hh[r * k + l], hl[r * k + l], a, b, sh, chh);
+            }
             const int64_t e = (i0 + r) * k + j;
-            // s + a = u + v exactly (TwoSum), then one float64 addition
-            const float a = A[e];
-            const float u = __fadd_rn(s, a);
-            const float ba = __fsub_rn(u, s);
-            const float v = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, ba)), __fsub_rn(a, ba)), c);
-            Z[e] = df_to_f64(u) + df_to_f64(v);
-            Z32[e] = __fadd_rn(u, v);
+            // + P, + HP: TwoSum with the high word, the rest into the low word
+            auto add = [](float s, float c, float a, float &u, float &v) {
+                u = __fadd_rn(s, a);
+                const float ba = __fsub_rn(u, s);
+                v = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, ba)), __fsub_rn(a, ba)), c);
+            };
+            float ux, vx, uh, vh;
+            add(sx, cx, P[e], ux, vx);
+            add(sh, chh, HP[e], uh, vh);
+            X[e] = df_to_f64(ux) + df_to_f64(vx);
+            HX[e] = df_to_f64(uh) + df_to_f64(vh);
+            const float x32 = __fadd_rn(ux, vx);
+            X32[e] = x32;
+            HX32[e] = __fadd_rn(uh, vh);
+            // r = hx - x theta: x theta = p + ep + cross (p = fl(ux th_h), exact with ep)
+            const float p = __fmul_rn(ux, th_h);
+            const float ep = __fmaf_rn(ux, th_h, -p);
+            const float cross = __fmaf_rn(ux, th_l, __fmul_rn(vx, th_h));
+            float a0, a1;
+            add(uh, vh, -p, a0, a1);
+            const float rf = __fadd_rn(a0, __fsub_rn(a1, __fadd_rn(ep, cross)));
+            R32[e] = rf;
+            float w = rf;
+            if (mode == 1) {
+                const float t = __fsub_rn(d[i0 + r], thf);
+                const float g = (t >= 0.f) ? fmaxf(t, delta) : -fmaxf(-t, delta);
+                w = w / g;
+            }
+            W[e] = w;
+            rr = __fmaf_rn(rf, rf, rr);
+            xx = __fmaf_rn(x32, x32, xx);
         }
     }
+    if (active) {
+        atomicAdd(&red[j], static_cast<double>(rr));
+        atomicAdd(&red[k + j], static_cast<double>(xx));
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) atomicAdd(&norms[q], red[q]);
 }
 
 constexpr int GX_THREADS = 256;
-constexpr int GX_ROWS = 64;     // rows staged per pass (and folded into float64 per pass)
-constexpr int GX_MAXE = 8;      // entries per thread: 2 k^2 <= 8 * 256 (k <= 32)
+constexpr int GX_ROWS = 128;    // rows staged per pass (and folded into float64 per pass)
 
-// G[i][j] = sum_r X[r][i] B[r][j], B = [HX X]: thread t owns entries
-// t + 256 q; the CTA's rows in passes of 64, split into shared memory
+// G = X^T [HX X] (k x 2k) with both k x k blocks symmetric: only their lower
+// triangles are summed (H is symmetric, so X^T HX is in exact arithmetic)
+// and mirrored on output.  The k columns are padded to kp (even) and each
+// block's lower triangle covered by 2 x 2 sub-blocks ("units": U = 2 T,
+// T = nb (nb + 1) / 2, nb = kp / 2); thread L (of `groups` x U, UPT units a
+// thread) owns unit L % U and takes the pass's rows g, g + groups, ...
+// (g = L / U), four df_mac per row from two float2 loads of each operand.
+template <int UPT>
 __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, const double *X, const double *HX,
                                                           double *G) {
-    extern __shared__ float gs[];   // xh, xl, yh, yl: GX_ROWS x k each (y = HX rows)
-    float *xh = gs, *xl = gs + GX_ROWS * k, *yh = gs + 2 * GX_ROWS * k, *yl = gs + 3 * GX_ROWS * k;
-    const int ne = 2 * k * k;
-    double acc[GX_MAXE];
-    float s[GX_MAXE], c[GX_MAXE];
+    extern __shared__ float gs[];   // xh, xl, yh, yl: GX_ROWS x kp each (y = HX rows)
+    const int kp = (k + 1) & ~1, nb = kp / 2, T = nb * (nb + 1) / 2, U = 2 * T;
+    const int groups = U <= GX_THREADS ? GX_THREADS / U : 1;
+    float *xh = gs, *xl = gs + GX_ROWS * kp, *yh = gs + 2 * GX_ROWS * kp, *yl = gs + 3 * GX_ROWS * kp;
+    for (int q = threadIdx.x; q < 4 * GX_ROWS * kp; q += blockDim.x) gs[q] = 0.f;   // padding columns stay 0
+    int grp[UPT], ia[UPT], ib[UPT];
+    bool hxb[UPT], valid[UPT];
+    double acc[UPT][4];
+    float sv[UPT][4], cv[UPT][4];
 #pragma unroll
-    for (int q = 0; q < GX_MAXE; ++q) {
-        acc[q] = 0.0;
-        s[q] = c[q] = 0.f;
+    for (int q = 0; q < UPT; ++q) {
+        const int L = threadIdx.x + GX_THREADS * q;
+        grp[q] = L / U;
+        valid[q] = grp[q] < groups;
+        int t = L % U;
+        hxb[q] = t < T;
+        if (!hxb[q]) t -= T;
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        ia[q] = 2 * bi;
+        ib[q] = 2 * (t - bi * (bi + 1) / 2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            acc[q][e] = 0.0;
+            sv[q][e] = cv[q][e] = 0.f;
+        }
     }
     const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per_cta;
@@ -78,29 +157,59 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
         const int rows = static_cast<int>(std::min<int64_t>(GX_ROWS, r1 - a));
         __syncthreads();
         for (int q = threadIdx.x; q < rows * k; q += blockDim.x) {
-            df_split(X[a * k + q], xh[q], xl[q]);
-            df_split(HX[a * k + q], yh[q], yl[q]);
+            const int r = q / k, c = q - r * k;
+            df_split(X[a * k + q], xh[r * kp + c], xl[r * kp + c]);
+            df_split(HX[a * k + q], yh[r * kp + c], yl[r * kp + c]);
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < GX_MAXE; ++q) {
-            const int en = threadIdx.x + GX_THREADS * q;
-            if (en < ne) {
-                const int i = en / (2 * k), jj = en % (2 * k);
-                const bool hxcol = jj < k;
-                const int j = hxcol ? jj : jj - k;
-                const float *bh = hxcol ? yh : xh, *bl = hxcol ? yl : xl;
-                for (int r = 0; r < rows; ++r)
-                    df_mac(xh[r * k + i], xl[r * k + i], bh[r * k + j], bl[r * k + j], s[q], c[q]);
-                acc[q] += df_to_f64(s[q]) + df_to_f64(c[q]);
-                s[q] = c[q] = 0.f;
+        for (int q = 0; q < UPT; ++q) {
+            if (!valid[q]) continue;
+            const float *bh = hxb[q] ? yh : xh, *bl = hxb[q] ? yl : xl;
+            for (int r = grp[q]; r < rows; r += groups) {
+                const float2 ah = *reinterpret_cast<const float2 *>(xh + r * kp + ia[q]);
+                const float2 al = *reinterpret_cast<const float2 *>(xl + r * kp + ia[q]);
+                const float2 h2 = *reinterpret_cast<const float2 *>(bh + r * kp + ib[q]);
+                const float2 l2 = *reinterpret_cast<const float2 *>(bl + r * kp + ib[q]);
+                df_mac(ah.x, al.x, h2.x, l2.x, sv[q][0], cv[q][0]);
+                df_mac(ah.x, al.x, h2.y, l2.y, sv[q][1], cv[q][1]);
+                df_mac(ah.y, al.y, h2.x, l2.x, sv[q][2], cv[q][2]);
+                df_mac(ah.y, al.y, h2.y, l2.y, sv[q][3], cv[q][3]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                acc[q][e] += df_to_f64(sv[q][e]) + df_to_f64(cv[q][e]);
+                sv[q][e] = cv[q][e] = 0.f;
             }
         }
     }
+    // sum the groups' partials in shared memory, then one atomic per entry
+    // (and its mirror)
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(gs);   // [groups][U][4]
 #pragma unroll
-    for (int q = 0; q < GX_MAXE; ++q) {
-        const int en = threadIdx.x + GX_THREADS * q;
-        if (en < ne && r0 < r1) atomicAdd(&G[en], acc[q]);
+    for (int q = 0; q < UPT; ++q) {
+        if (!valid[q]) continue;
+        const int L = threadIdx.x + GX_THREADS * q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red[L * 4 + e] = acc[q][e];
+    }
+    __syncthreads();
+    if (r0 >= r1) return;
+    for (int v = threadIdx.x; v < 4 * U; v += blockDim.x) {
+        double sum = 0.0;
+        for (int g = 0; g < groups; ++g) sum += red[g * 4 * U + v];
+        const int u = v / 4, e = v % 4;
+        int t = u;
+        const bool hx = t < T;
+        if (!hx) t -= T;
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int i = 2 * bi + (e >> 1), j = 2 * (t - bi * (bi + 1) / 2) + (e & 1);
+        if (i >= k || j > i) continue;
+        const int off = hx ? 0 : k;
+        atomicAdd(&G[i * 2 * k + off + j], sum);
+        if (j != i) atomicAdd(&G[j * 2 * k + off + i], sum);
     }
 }
 
@@ -108,14 +217,17 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
 
 bool mixed_df_ok(int k) { return k >= 1 && k <= 32; }
 
-cudaError_t launch_xupdate_df(int64_t n, int k, double *Z, const double *C, const float *A, float *Z32, int num_sms,
-                              cudaStream_t s) {
+cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, const float *P,
+                               const float *HP, float *X32, float *HX32, const double *theta, const float *d,
+                               float *W, float *R32, int mode, double *norms, int num_sms, cudaStream_t s) {
     if (!mixed_df_ok(k)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * k, s);
+    if (e != cudaSuccess) return e;
     const int per = XU_THREADS / k;
-    const size_t smem = sizeof(float) * (2 * k * k + 2 * per * k);
+    const size_t smem = sizeof(float) * (2 * k * k + 4 * per * k);
     int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
     if (blocks < 1) blocks = 1;
-    k_xupdate_df<<<blocks, XU_THREADS, smem, s>>>(n, k, Z, C, A, Z32);
+    k_xupdate2_df<<<blocks, XU_THREADS, smem, s>>>(n, k, X, HX, C, P, HP, X32, HX32, theta, d, W, R32, mode, norms);
     return cudaGetLastError();
 }
 
@@ -124,10 +236,21 @@ cudaError_t launch_gram_x_df(int64_t n, int k, const double *X, const double *HX
     if (!mixed_df_ok(k)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * 2 * k * k, s);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * 4 * GX_ROWS * k;
-    int blocks = static_cast<int>(std::min<int64_t>((n + GX_ROWS - 1) / GX_ROWS, static_cast<int64_t>(num_sms) * 2));
+    const int kp = (k + 1) & ~1, nb = kp / 2, U = nb * (nb + 1);
+    const int groups = U <= GX_THREADS ? GX_THREADS / U : 1;
+    // the staged rows, later the [groups][U][4] float64 partials
+    const size_t smem = std::max(sizeof(float) * 4 * GX_ROWS * kp, sizeof(double) * 4 * groups * U);
+    int blocks = static_cast<int>(std::min<int64_t>((n + GX_ROWS - 1) / GX_ROWS, static_cast<int64_t>(num_sms) * 3));
     if (blocks < 1) blocks = 1;
-    k_gram_x_df<<<blocks, GX_THREADS, smem, s>>>(n, k, X, HX, G);
+    if (U <= GX_THREADS) {
+        e = cudaFuncSetAttribute(k_gram_x_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        k_gram_x_df<1><<<blocks, GX_THREADS, smem, s>>>(n, k, X, HX, G);
+    } else {
+        e = cudaFuncSetAttribute(k_gram_x_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        k_gram_x_df<2><<<blocks, GX_THREADS, smem, s>>>(n, k, X, HX, G);
+    }
     return cudaGetLastError();
 }
 

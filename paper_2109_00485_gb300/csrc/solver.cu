@@ -555,8 +555,8 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
     CK(spmm_T<T>(h, b.X, b.HX, k));
     CK(rr_on_x<T>(h, s, b));
     bool hasP = false;
-    double best = INFINITY;
-    int since_best = 0;
+    double best = INFINITY, floor_best = INFINITY;
+    int since_best = 0, since_floor = 0;
     int restarts = 0;
     std::vector<double> rho, theta;
     bool resid_ready = false;   // the last iteration's fused update formed R (and W)
@@ -600,17 +600,27 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
             CK(cudaMemcpyAsync(b.HX, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             continue;
         }
-        // Stagnation (15 iterations without a 0.7x improvement) or growth
+        // Stagnation (15 iterations without a 0.7x improvement), growth
         // (4x above a best below 1e-3: at the float32 rounding floor the
         // HX/HP recurrences lose consistency and the residual grows
-        // geometrically) ends a phase that can be continued in higher
-        // precision; it then hands over the best X it has seen.
+        // geometrically) or a floor (below 1e-2, no new minimum by 5 % in 3
+        // iterations: the residual only fluctuates around the rounding
+        // level, while a slow but converging run still gains 5 % an
+        // iteration) ends a phase that can be continued in higher
+        // precision; it then hands over the X of the lowest residual seen.
+        if (worst < 0.95 * floor_best) {
+            floor_best = worst;
+            since_floor = 0;
+            if (stop_on_stagnation && snap)
+                CK(cudaMemcpyAsync(snap, b.X, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+            ++since_floor;
+        }
         if (worst < 0.7 * best) {
             best = worst;
             since_best = 0;
-            if (stop_on_stagnation && snap)
-                CK(cudaMemcpyAsync(snap, b.X, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
-        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best))) {
+        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best) ||
+                                          (floor_best < 1e-2 && since_floor >= 3))) {
             res.stagnated = true;
             if (snap) CK(cudaMemcpyAsync(b.X, snap, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             break;
@@ -682,9 +692,12 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
     std::vector<double> rho, theta;
     int restarts = 0, refreshes = 0, since_best = 0;
     double best = INFINITY;
+    bool resid_ready = false;   // the previous iteration's update formed this residual
     while (true) {
-        CK(launch_resid_mixed(n, k, d.X, d.HX, s->theta, h->T.diag, f.W, R32, pmode == 1 ? 1 : 0, s->norms,
-                              h->num_sms, h->stream));
+        if (!resid_ready)
+            CK(launch_resid_mixed(n, k, d.X, d.HX, s->theta, h->T.diag, f.W, R32, pmode == 1 ? 1 : 0, s->norms,
+                                  h->num_sms, h->stream));
+        resid_ready = false;
         int rr_st = 0, orth_st = 0;
         CK(read_progress<float>(h, s, rho, theta, &rr_st, &orth_st, st));
         trace("mixed", res.iters, rho, theta, nev, rr_st);
@@ -783,8 +796,10 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
         CK(launch_combine<float>(n, k, na - 1, aWP, 1, op, s->colsqP, h->num_sms, h->stream));
         CK(launch_combine<float>(n, k, na - 1, aHWP, 1, ohp, nullptr, h->num_sms, h->stream));
         if (mixed_df_ok(k)) {
-            CK(launch_xupdate_df(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
-            CK(launch_xupdate_df(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
+            // both updates and the next iteration's residual in one pass
+            CK(launch_xupdate2_df(n, k, d.X, d.HX, s->C, f.P, f.HP, f.X, f.HX, s->theta, h->T.diag, f.W, R32,
+                                  pmode == 1 ? 1 : 0, s->norms, h->num_sms, h->stream));
+            resid_ready = true;
         } else {
             CK(launch_xupdate(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
             CK(launch_xupdate(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
@@ -1044,8 +1059,8 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
     CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
     CK(dav_orth<T>(h, s, D, V, 0, V[0]));
     CK(spmm_T<T>(h, V[0], HV[0], k));
-    int nb = 1, restarts = 0, since_best = 0;
-    double best = INFINITY;
+    int nb = 1, restarts = 0, since_best = 0, since_floor = 0;
+    double best = INFINITY, floor_best = INFINITY;
     std::vector<double> rho, theta;
     while (true) {
         const int m = nb * k;
@@ -1102,11 +1117,19 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
             continue;
         }
         // a float32 run hands over once its residual stalls (15 iterations
-        // without a 0.7x gain) or grows 4x above a best below 1e-3
+        // without a 0.7x gain), grows 4x above a best below 1e-3 or sits at
+        // a floor (below 1e-2, no new 5 % minimum in 3 iterations)
+        if (worst < 0.95 * floor_best) {
+            floor_best = worst;
+            since_floor = 0;
+        } else {
+            ++since_floor;
+        }
         if (worst < 0.7 * best) {
             best = worst;
             since_best = 0;
-        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best))) {
+        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best) ||
+                                          (floor_best < 1e-2 && since_floor >= 3))) {
             res.stagnated = true;
             break;
         }

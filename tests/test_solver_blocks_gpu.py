@@ -83,6 +83,28 @@ def test_solve_block_sizes_match_oracle(k, nev, precond):
     check(A, k, nev, h, X0)
 
 
+@pytest.mark.parametrize("k,nev", [(7, 4), (32, 10)])
+def test_refinement_odd_and_largest_block(k, nev):
+    """A tolerance of 1e-9 is below the float32 phase's rounding floor, so
+    the solve goes through the float64 refinement: its Gram of X and HX
+    (lower triangles on 2 x 2 sub-blocks, columns padded to an even count
+    at k = 7, two sub-blocks on some threads at k = 32) and its fused
+    update-and-residual kernel.  Eigenvalues within 1e-8, float64 residuals
+    of the returned vectors within the tolerance."""
+    pkg = _pkg()
+    A = matrix()
+    X0 = synth.initial_guess(A, k, seed=1003, fp32=True)
+    h = pkg.from_csr(A, k=k, nev=nev, tol=1e-9, maxiter=2000, precond="diag", polish_fp64=1)
+    X, ev, rs, st = h.solve(X0)
+    X64 = h.get_x_f64().cpu().numpy()
+    h.destroy()
+    assert st["converged"] == 1 and st["used_fp64"] == 1 and st["iters_fp64"] > 0, st
+    err = eig_err(ev, reference(nev), oracle.gershgorin(A))
+    assert np.all(err <= 1e-8), err
+    rho = residuals_fp64(A, X64[:, :nev], ev)
+    assert np.all(rho <= 1.05e-9), rho
+
+
 def test_oracle_lobpcg_agrees_with_dense_reference():
     """The oracle's LOBPCG (explicit products, tol 1e-10) on the same matrix
     at k = 20 gives the dense eigenvalues: the two references agree."""
