@@ -251,7 +251,15 @@ class Handle:
             if X.shape != (self.n, k):
                 raise ValueError(f"X0 must be ({self.n}, {k})")
         else:
-            X = X0.detach().clone().contiguous()
+            import torch
+            if X0.is_cuda and self.stream is not None:
+                # the copy on the handle's stream, after the caller's stream
+                # has produced X0
+                self.stream.wait_stream(torch.cuda.current_stream(X0.device))
+                with torch.cuda.stream(self.stream):
+                    X = X0.detach().clone().contiguous()
+            else:
+                X = X0.detach().clone().contiguous()
             if tuple(X.shape) != (self.n, k) or str(X.dtype) != "torch.float32":
                 raise ValueError(f"X0 must be float32 ({self.n}, {k})")
         ev = np.zeros(nev)
