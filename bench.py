@@ -565,6 +565,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true")
+    ap.add_argument("--forms", default="diag,bjacobi,fom,fom_var,mlp,davidson_diag",
+                    help="comma-separated solve forms of the lobpcg sub-record")
     ap.add_argument("--solve-repeats", type=int, default=3, help="solves per preconditioner form (median reported)")
     ap.add_argument("--no-largest", action="store_true", help="skip the n = 8M sub-record")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -659,7 +661,9 @@ def main():
 
     solves = None
     if rank == 0 and not args.no_solves:
-        solves = lobpcg_solves(pkg, A, p, stream, repeats=args.solve_repeats, gold=golden_evals(args.workload))
+        forms = tuple(f for f in args.forms.split(",") if f)
+        solves = lobpcg_solves(pkg, A, p, stream, precs=forms, repeats=args.solve_repeats,
+                               gold=golden_evals(args.workload))
     fom = None
     if rank == 0 and not args.no_solves:
         fom = fom_report(pkg, A, p, stream, peaks["sm_max_mhz"])
