@@ -53,14 +53,32 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
     // hundred at most: relative error below 1e-4, enough for the norms'
     // use in the convergence test), folded into float64 once at the end
     float rr = 0.f, xx = 0.f;
-    for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * per; i0 < n; i0 += static_cast<int64_t>(gridDim.x) * per) {
+    // a pass's inputs are loaded during the pass before (thread r k + j
+    // loads element (r, j) of X and HX, which it also updates)
+    const int64_t step = static_cast<int64_t>(gridDim.x) * per;
+    double fx = 0.0, fh = 0.0;
+    float fp = 0.f, fhp = 0.f, fd = 0.f;
+    auto fetch = [&](int64_t i) {
+        const int rws = static_cast<int>(n - i < per ? n - i : per);
+        if (threadIdx.x < rws * k) {
+            fx = X[i * k + threadIdx.x];
+            fh = HX[i * k + threadIdx.x];
+            fp = P[i * k + threadIdx.x];
+            fhp = HP[i * k + threadIdx.x];
+            if (mode == 1) fd = d[i + r];
+        }
+    };
+    if (static_cast<int64_t>(blockIdx.x) * per < n) fetch(static_cast<int64_t>(blockIdx.x) * per);
+    for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * per; i0 < n; i0 += step) {
         const int rows = static_cast<int>(n - i0 < per ? n - i0 : per);
+        const float pe = fp, hpe = fhp, de = fd;
         __syncthreads();
         if (threadIdx.x < rows * k) {
-            df_split(X[i0 * k + threadIdx.x], xh[threadIdx.x], xl[threadIdx.x]);
-            df_split(HX[i0 * k + threadIdx.x], hh[threadIdx.x], hl[threadIdx.x]);
+            df_split(fx, xh[threadIdx.x], xl[threadIdx.x]);
+            df_split(fh, hh[threadIdx.x], hl[threadIdx.x]);
         }
         __syncthreads();
+        if (i0 + step < n) fetch(i0 + step);
         if (active && r < rows) {
             float sx = 0.f, cx = 0.f, sh = 0.f, chh = 0.f;
             for (int l = 0; l < k; ++l) {
@@ -76,8 +94,8 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
                 v = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, ba)), __fsub_rn(a, ba)), c);
             };
             float ux, vx, uh, vh;
-            add(sx, cx, P[e], ux, vx);
-            add(sh, chh, HP[e], uh, vh);
+            add(sx, cx, pe, ux, vx);
+            add(sh, chh, hpe, uh, vh);
             X[e] = df_to_f64(ux) + df_to_f64(vx);
             HX[e] = df_to_f64(uh) + df_to_f64(vh);
             const float x32 = __fadd_rn(ux, vx);
@@ -93,7 +111,7 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
             R32[e] = rf;
             float w = rf;
             if (mode == 1) {
-                const float t = __fsub_rn(d[i0 + r], thf);
+                const float t = __fsub_rn(de, thf);
                 const float g = (t >= 0.f) ? fmaxf(t, delta) : -fmaxf(-t, delta);
                 w = w / g;
             }
@@ -111,7 +129,8 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
 }
 
 constexpr int GX_THREADS = 256;
-constexpr int GX_ROWS = 128;    // rows staged per pass (and folded into float64 per pass)
+constexpr int GX_ROWS = 128;    // rows staged per pass at most (and folded into float64 per pass)
+constexpr int GX_PER = 8;       // values of X (and of HX) a thread loads per pass: rows x k <= 8 x 256
 
 // G = X^T [HX X] (k x 2k) with both k x k blocks symmetric: only their lower
 // triangles are summed (H is symmetric, so X^T HX is in exact arithmetic)
@@ -153,15 +172,34 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
     const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per_cta;
     const int64_t r1 = std::min<int64_t>(n, r0 + per_cta);
-    for (int64_t a = r0; a < r1; a += GX_ROWS) {
-        const int rows = static_cast<int>(std::min<int64_t>(GX_ROWS, r1 - a));
+    const int RP = GX_PER * GX_THREADS / k < GX_ROWS ? GX_PER * GX_THREADS / k : GX_ROWS;   // rows per pass
+    // a pass's rows are loaded into registers during the pass before
+    double px[GX_PER], ph[GX_PER];
+    auto fetch = [&](int64_t a, int rows) {
+#pragma unroll
+        for (int t = 0; t < GX_PER; ++t) {
+            const int q = threadIdx.x + GX_THREADS * t;
+            if (q < rows * k) {
+                px[t] = X[a * k + q];
+                ph[t] = HX[a * k + q];
+            }
+        }
+    };
+    if (r0 < r1) fetch(r0, static_cast<int>(std::min<int64_t>(RP, r1 - r0)));
+    for (int64_t a = r0; a < r1; a += RP) {
+        const int rows = static_cast<int>(std::min<int64_t>(RP, r1 - a));
         __syncthreads();
-        for (int q = threadIdx.x; q < rows * k; q += blockDim.x) {
-            const int r = q / k, c = q - r * k;
-            df_split(X[a * k + q], xh[r * kp + c], xl[r * kp + c]);
-            df_split(HX[a * k + q], yh[r * kp + c], yl[r * kp + c]);
+#pragma unroll
+        for (int t = 0; t < GX_PER; ++t) {
+            const int q = threadIdx.x + GX_THREADS * t;
+            if (q < rows * k) {
+                const int r = q / k, c = q - r * k;
+                df_split(px[t], xh[r * kp + c], xl[r * kp + c]);
+                df_split(ph[t], yh[r * kp + c], yl[r * kp + c]);
+            }
         }
         __syncthreads();
+        if (a + RP < r1) fetch(a + RP, static_cast<int>(std::min<int64_t>(RP, r1 - a - RP)));
 #pragma unroll
         for (int q = 0; q < UPT; ++q) {
             if (!valid[q]) continue;
