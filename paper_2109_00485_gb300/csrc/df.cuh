@@ -66,4 +66,51 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
     c = __fadd_rn(c, __fadd_rn(t, __fadd_rn(e, x)));
 }
 
+// Packed pairs (f32x2 instructions; each half rounds to nearest as its
+// scalar counterpart, and the explicit rounding mode keeps the compiler from
+// contracting them).
+#define LOBPCG_DF2_OP(name, op)                                                       \
+    __device__ __forceinline__ float2 name(float2 a, float2 b) {                      \
+        float2 r;                                                                     \
+        asm("{\n\t.reg .b64 ra, rb, rd;\n\t"                                          \
+            "mov.b64 ra, {%2, %3};\n\t"                                               \
+            "mov.b64 rb, {%4, %5};\n\t" op " rd, ra, rb;\n\t"                        \
+            "mov.b64 {%0, %1}, rd;\n\t}"                                              \
+            : "=f"(r.x), "=f"(r.y)                                                    \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                \
+        return r;                                                                     \
+    }
+LOBPCG_DF2_OP(df2_add, "add.rn.f32x2")
+LOBPCG_DF2_OP(df2_sub, "sub.rn.f32x2")
+LOBPCG_DF2_OP(df2_mul, "mul.rn.f32x2")
+#undef LOBPCG_DF2_OP
+__device__ __forceinline__ float2 df2_fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
+// df_mac on two independent pairs at once: (s, c) += (ah + al)(bh + bl)
+// per half, nbh = -bh.  Same steps as df_mac with q = -p: e = ah bh + q
+// exactly, TwoSum(s, -q) = (s - q, (s - (sn - bp)) - (q + bp)); each half
+// gives the bits df_mac gives.
+__device__ __forceinline__ void df_mac2(float2 ah, float2 al, float2 bh, float2 nbh, float2 bl, float2 &s,
+                                        float2 &c) {
+    const float2 q = df2_mul(ah, nbh);
+    const float2 e = df2_fma(ah, bh, q);
+    const float2 x = df2_fma(ah, bl, df2_mul(al, bh));
+    const float2 sn = df2_sub(s, q);
+    const float2 bp = df2_sub(sn, s);
+    const float2 t = df2_sub(df2_sub(s, df2_sub(sn, bp)), df2_add(q, bp));
+    s = sn;
+    c = df2_add(c, df2_add(t, df2_add(e, x)));
+}
+
 }  // namespace lobpcg

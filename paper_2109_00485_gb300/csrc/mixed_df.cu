@@ -36,12 +36,20 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
                                                             const float *P, const float *HP, float *X32, float *HX32,
                                                             const double *theta, const float *d, float *W, float *R32,
                                                             int mode, double *norms) {
-    extern __shared__ float xs[];   // ch, cl (k x k), xh, xl, hh, hl (per x k each)
+    // C's words as duplicated pairs (c, c), (-c, -c), (c_lo, c_lo) (k x k
+    // each); a row element of X and HX as the pairs (x_hi, hx_hi), (x_lo,
+    // hx_lo) (per x k each): one packed df_mac2 updates x and hx together
+    extern __shared__ float2 xs2[];
     __shared__ double red[64];      // [2k]
     const int per = XU_THREADS / k;
-    float *ch = xs, *cl = xs + k * k, *xh = xs + 2 * k * k, *xl = xh + per * k, *hh = xl + per * k,
-          *hl = hh + per * k;
-    for (int q = threadIdx.x; q < k * k; q += blockDim.x) df_split(C[q], ch[q], cl[q]);
+    float2 *cp = xs2, *cn = xs2 + k * k, *cl = xs2 + 2 * k * k, *zh = xs2 + 3 * k * k, *zl = zh + per * k;
+    for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+        float a, b;
+        df_split(C[q], a, b);
+        cp[q] = make_float2(a, a);
+        cn[q] = make_float2(-a, -a);
+        cl[q] = make_float2(b, b);
+    }
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) red[q] = 0.0;
     const int r = threadIdx.x / k, j = threadIdx.x % k;
     const bool active = r < per;
@@ -74,18 +82,19 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
         const float pe = fp, hpe = fhp, de = fd;
         __syncthreads();
         if (threadIdx.x < rows * k) {
-            df_split(fx, xh[threadIdx.x], xl[threadIdx.x]);
-            df_split(fh, hh[threadIdx.x], hl[threadIdx.x]);
+            float a, b, c, e;
+            df_split(fx, a, b);
+            df_split(fh, c, e);
+            zh[threadIdx.x] = make_float2(a, c);
+            zl[threadIdx.x] = make_float2(b, e);
         }
         __syncthreads();
         if (i0 + step < n) fetch(i0 + step);
         if (active && r < rows) {
-            float sx = 0.f, cx = 0.f, sh = 0.f, chh = 0.f;
-            for (int l = 0; l < k; ++l) {
-                const float a = ch[l * k + j], b = cl[l * k + j];
-                df_mac(xh[r * k + l], xl[r * k + l], a, b, sx, cx);
-                df_mac(hh[r * k + l], hl[r * k + l], a, b, sh, chh);
-            }
+            float2 s2 = make_float2(0.f, 0.f), c2 = s2;   // (x, hx) sums and compensations
+            for (int l = 0; l < k; ++l)
+                df_mac2(zh[r * k + l], zl[r * k + l], cp[l * k + j], cn[l * k + j], cl[l * k + j], s2, c2);
+            const float sx = s2.x, cx = c2.x, sh = s2.y, chh = c2.y;
             const int64_t e = (i0 + r) * k + j;
             // + P, + HP: TwoSum with the high word, the rest into the low word
             auto add = [](float s, float c, float a, float &u, float &v) {
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
     int grp[UPT], ia[UPT], ib[UPT];
     bool hxb[UPT], valid[UPT];
     double acc[UPT][4];
-    float sv[UPT][4], cv[UPT][4];
+    float2 sv[UPT][2], cv[UPT][2];   // entries (0, 1) and (2, 3) of a unit as packed pairs
 #pragma unroll
     for (int q = 0; q < UPT; ++q) {
         const int L = threadIdx.x + GX_THREADS * q;
@@ -164,10 +173,8 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
         ia[q] = 2 * bi;
         ib[q] = 2 * (t - bi * (bi + 1) / 2);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            acc[q][e] = 0.0;
-            sv[q][e] = cv[q][e] = 0.f;
-        }
+        for (int e = 0; e < 4; ++e) acc[q][e] = 0.0;
+        sv[q][0] = sv[q][1] = cv[q][0] = cv[q][1] = make_float2(0.f, 0.f);
     }
     const int64_t per_cta = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * per_cta;
@@ -209,15 +216,15 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
                 const float2 al = *reinterpret_cast<const float2 *>(xl + r * kp + ia[q]);
                 const float2 h2 = *reinterpret_cast<const float2 *>(bh + r * kp + ib[q]);
                 const float2 l2 = *reinterpret_cast<const float2 *>(bl + r * kp + ib[q]);
-                df_mac(ah.x, al.x, h2.x, l2.x, sv[q][0], cv[q][0]);
-                df_mac(ah.x, al.x, h2.y, l2.y, sv[q][1], cv[q][1]);
-                df_mac(ah.y, al.y, h2.x, l2.x, sv[q][2], cv[q][2]);
-                df_mac(ah.y, al.y, h2.y, l2.y, sv[q][3], cv[q][3]);
+                const float2 nh2 = make_float2(-h2.x, -h2.y);
+                df_mac2(make_float2(ah.x, ah.x), make_float2(al.x, al.x), h2, nh2, l2, sv[q][0], cv[q][0]);
+                df_mac2(make_float2(ah.y, ah.y), make_float2(al.y, al.y), h2, nh2, l2, sv[q][1], cv[q][1]);
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                acc[q][e] += df_to_f64(sv[q][e]) + df_to_f64(cv[q][e]);
-                sv[q][e] = cv[q][e] = 0.f;
+            for (int e2 = 0; e2 < 2; ++e2) {
+                acc[q][2 * e2] += df_to_f64(sv[q][e2].x) + df_to_f64(cv[q][e2].x);
+                acc[q][2 * e2 + 1] += df_to_f64(sv[q][e2].y) + df_to_f64(cv[q][e2].y);
+                sv[q][e2] = cv[q][e2] = make_float2(0.f, 0.f);
             }
         }
     }
@@ -262,7 +269,7 @@ cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const do
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * k, s);
     if (e != cudaSuccess) return e;
     const int per = XU_THREADS / k;
-    const size_t smem = sizeof(float) * (2 * k * k + 4 * per * k);
+    const size_t smem = sizeof(float2) * (3 * k * k + 2 * per * k);
     int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
     if (blocks < 1) blocks = 1;
     k_xupdate2_df<<<blocks, XU_THREADS, smem, s>>>(n, k, X, HX, C, P, HP, X32, HX32, theta, d, W, R32, mode, norms);
