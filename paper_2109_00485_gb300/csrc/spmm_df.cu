@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "df.cuh"
 #include "internal.h"
 
 namespace lobpcg {
@@ -55,21 +56,24 @@ __global__ void k_split64(int64_t m, int64_t mp, const double *x, float *xh, flo
     }
 }
 
-// s + c += h (x_hi + x_lo), see the file comment; intrinsics keep the
-// compiler from contracting or reassociating the error-free steps
-__device__ __forceinline__ void df_term(float h, float xh, float xl, float &s, float &c) {
-    const float p = __fmul_rn(h, xh);
-    const float e = __fmaf_rn(h, xh, -p);
-    const float sn = __fadd_rn(s, p);
-    const float bp = __fsub_rn(sn, s);
-    const float t = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+// s + c += h (x_hi + x_lo) (the file comment's steps) for two outputs at
+// once, as packed f32x2 instructions (each half rounds as the scalar
+// operation, and the explicit rounding keeps the compiler from contracting
+// or reassociating the error-free steps): hh = (h, h), nh = (-h, -h),
+// q = -p, TwoSum(s, p) written as (s - q, (s - (sn - bp)) - (q + bp))
+__device__ __forceinline__ void df_term2(float2 hh, float2 nh, float2 xh, float2 xl, float2 &s, float2 &c) {
+    const float2 q = df2_mul(nh, xh);
+    const float2 e = df2_fma(hh, xh, q);
+    const float2 sn = df2_sub(s, q);
+    const float2 bp = df2_sub(sn, s);
+    const float2 t = df2_sub(df2_sub(s, df2_sub(sn, bp)), df2_add(q, bp));
     s = sn;
-    c = __fmaf_rn(h, xl, __fadd_rn(c, __fadd_rn(t, e)));
+    c = df2_fma(hh, xl, df2_add(c, df2_add(t, e)));
 }
 
-__device__ __forceinline__ void df_renorm(float &s, float &c) {
-    const float sn = __fadd_rn(s, c);
-    c = __fsub_rn(c, __fsub_rn(sn, s));
+__device__ __forceinline__ void df_renorm2(float2 &s, float2 &c) {
+    const float2 sn = df2_add(s, c);
+    c = df2_sub(c, df2_sub(sn, s));
     s = sn;
 }
 
@@ -157,21 +161,47 @@ __device__ __forceinline__ int df_stage(const DfPrefetch<K> &f, DfWarp *ws, int 
 }
 
 // acc[q] (+)= sum_t A(o, t) x[t][q0 + q], o = lane / 2, q0 = (lane % 2) K / 2;
-// A(o, t) = tile[o][t] (rows pass) or tile[t][o] (columns pass)
+// A(o, t) = tile[o][t] (rows pass) or tile[t][o] (columns pass).  The
+// outputs in packed pairs (q, q + 1); for odd K / 2 the last pair's second
+// half runs on a neighbouring column and is never written.
+template <int K>
+struct DfAcc {
+    static constexpr int KP = (K / 2 + 1) / 2;
+    float2 s[KP], c[KP];
+};
 template <int K, bool TRANS>
-__device__ __forceinline__ void df_mac(const DfWarp *ws, int lane, float (&s)[K / 2], float (&c)[K / 2]) {
-    constexpr int KH = K / 2;
+__device__ __forceinline__ void df_tile_mac(const DfWarp *ws, int lane, DfAcc<K> &acc) {
+    constexpr int KH = K / 2, KP = DfAcc<K>::KP;
     const int o = lane >> 1, q0 = (lane & 1) * KH;
 #pragma unroll 4
     for (int t = 0; t < TILE; ++t) {
         const float h = TRANS ? ws->ht[t * DF_HS + o] : ws->ht[o * DF_HS + t];
+        const float2 hh = make_float2(h, h), nh = make_float2(-h, -h);
         const float *ph = ws->xh + t * K + q0;
         const float *pl = ws->xl + t * K + q0;
 #pragma unroll
-        for (int q = 0; q < KH; ++q) df_term(h, ph[q], pl[q], s[q], c[q]);
+        for (int p = 0; p < KP; ++p) {
+            float2 xh2, xl2;
+            if constexpr (KH % 2 == 0) {
+                xh2 = reinterpret_cast<const float2 *>(ph)[p];
+                xl2 = reinterpret_cast<const float2 *>(pl)[p];
+            } else {
+                xh2 = make_float2(ph[2 * p], ph[2 * p + 1]);
+                xl2 = make_float2(pl[2 * p], pl[2 * p + 1]);
+            }
+            df_term2(hh, nh, xh2, xl2, acc.s[p], acc.c[p]);
+        }
     }
 #pragma unroll
-    for (int q = 0; q < KH; ++q) df_renorm(s[q], c[q]);
+    for (int p = 0; p < KP; ++p) df_renorm2(acc.s[p], acc.c[p]);
+}
+
+// output q of the lane's half (s + c as float64)
+template <int K>
+__device__ __forceinline__ double df_out(const DfAcc<K> &acc, int q) {
+    const float2 s = acc.s[q >> 1], c = acc.c[q >> 1];
+    return (q & 1) ? static_cast<double>(s.y) + static_cast<double>(c.y)
+                   : static_cast<double>(s.x) + static_cast<double>(c.x);
 }
 
 // Rows pass: Y[rb] = sum over rb's chunks of H_t X_C.
@@ -185,9 +215,9 @@ __global__ void __launch_bounds__(DF_WARPS * 32, 2) k_spmm_df_rows(int64_t n, in
     constexpr int KH = K / 2;
     for (int64_t rb = static_cast<int64_t>(blockIdx.x) * DF_WARPS + warp; rb < R;
          rb += static_cast<int64_t>(gridDim.x) * DF_WARPS) {
-        float s[KH], c[KH];
+        DfAcc<K> acc;
 #pragma unroll
-        for (int q = 0; q < KH; ++q) s[q] = c[q] = 0.f;
+        for (int q = 0; q < DfAcc<K>::KP; ++q) acc.s[q] = acc.c[q] = make_float2(0.f, 0.f);
         const int64_t c0 = rb_chunk[rb], c1 = rb_chunk[rb + 1];
         DfPrefetch<K> f;
         if (c0 < c1) {
@@ -201,13 +231,13 @@ __global__ void __launch_bounds__(DF_WARPS * 32, 2) k_spmm_df_rows(int64_t n, in
                 const int ct = __ldg(reinterpret_cast<const int4 *>(chunk + ci + 1)).z;
                 df_fetch<K>(f, data, chunk, ci + 1, static_cast<int64_t>(ct) * TILE, n, xh, xl, lane);
             }
-            df_mac<K, false>(ws, lane, s, c);
+            df_tile_mac<K, false>(ws, lane, acc);
         }
         const int o = lane >> 1, q0 = (lane & 1) * KH;
         const int64_t row = rb * TILE + o;
         if (row < n) {
 #pragma unroll
-            for (int q = 0; q < KH; ++q) Y[row * K + q0 + q] = static_cast<double>(s[q]) + static_cast<double>(c[q]);
+            for (int q = 0; q < KH; ++q) Y[row * K + q0 + q] = df_out<K>(acc, q);
         }
     }
 }
@@ -227,9 +257,9 @@ __global__ void __launch_bounds__(DF_WARPS * 32, 2) k_spmm_df_cols(int64_t n, in
          ct += static_cast<int64_t>(gridDim.x) * DF_WARPS) {
         const int64_t a0 = col_ptr[ct], a1 = col_ptr[ct + 1];
         if (a0 == a1) continue;
-        float s[KH], c[KH];
+        DfAcc<K> acc;
 #pragma unroll
-        for (int q = 0; q < KH; ++q) s[q] = c[q] = 0.f;
+        for (int q = 0; q < DfAcc<K>::KP; ++q) acc.s[q] = acc.c[q] = make_float2(0.f, 0.f);
         DfPrefetch<K> f;
         {
             const int2 e = __ldg(list + a0);
@@ -242,7 +272,7 @@ __global__ void __launch_bounds__(DF_WARPS * 32, 2) k_spmm_df_cols(int64_t n, in
                 const int2 e = __ldg(list + a + 1);
                 df_fetch<K>(f, data, chunk, e.x, static_cast<int64_t>(e.y) * TILE, n, xh, xl, lane);
             }
-            df_mac<K, true>(ws, lane, s, c);
+            df_tile_mac<K, true>(ws, lane, acc);
         }
         const int o = lane >> 1, q0 = (lane & 1) * KH;
         const int64_t row = ct * TILE + o;
@@ -250,7 +280,7 @@ __global__ void __launch_bounds__(DF_WARPS * 32, 2) k_spmm_df_cols(int64_t n, in
 #pragma unroll
             for (int q = 0; q < KH; ++q) {
                 double *y = Y + row * K + q0 + q;
-                *y = *y + (static_cast<double>(s[q]) + static_cast<double>(c[q]));
+                *y = *y + df_out<K>(acc, q);
             }
         }
     }
