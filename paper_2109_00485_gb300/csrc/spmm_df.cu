@@ -4,14 +4,14 @@
 //
 // GB300 issues FP64 at about 1/64 of its FP32 rate, so the products are
 // formed in float32 with error-free transformations instead:
-//   x = x_hi + x_lo        (x_hi = fl32(x), x_lo = fl32(x - x_hi); split once per call)
+//   x = x_hi + x_lo + d    (x_hi, x_lo the truncated 24-bit words, |d| < 2^-47 |x|; split once per call)
 //   h x_hi = p + e         (p = fl32(h x_hi), e = fma(h, x_hi, -p): exact, h being float32)
 //   s + p = s' + t         (TwoSum, Knuth: exact)
 //   c <- c + (t + e) + h x_lo
 // per term, with (s, c) renormalised by Fast2Sum after each 16-term tile.
-// Each term is then exact but for roundings of size 2^-48 |h x|, so an
-// output is within a few 2^-48 sum |h x| of its exact value; it is written
-// as the float64 s + c.
+// Each term is then exact but for the split's remainder and roundings of
+// size 2^-47 |h x|, so an output is within a few 2^-47 sum |h x| of its
+// exact value; it is written as the float64 s + c.
 //
 // Two passes, neither with atomics (so the result does not depend on the
 // order warps run in):
@@ -45,14 +45,16 @@ struct DfWarp {
     float xh[TILE * 32], xl[TILE * 32];   // 16 rows of x_hi, x_lo (row stride k)
 };
 
-// x = x_hi + x_lo for the m entries of x, zeros for entries m .. mp - 1
+// x = x_hi + x_lo for the m entries of x (df_split: integer operations on
+// the bit pattern, GB300 converting double to float at its FP64 rate),
+// zeros for entries m .. mp - 1
 __global__ void k_split64(int64_t m, int64_t mp, const double *x, float *xh, float *xl) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < mp;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const double v = (i < m) ? x[i] : 0.0;
-        const float hi = __double2float_rn(v);
+        float hi = 0.f, lo = 0.f;
+        if (i < m) df_split(x[i], hi, lo);
         xh[i] = hi;
-        xl[i] = __double2float_rn(v - static_cast<double>(hi));
+        xl[i] = lo;
     }
 }
 
