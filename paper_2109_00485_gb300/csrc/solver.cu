@@ -72,6 +72,16 @@ struct DavState {
     double *Cp = nullptr;   // (k + m) x k: [I; -B]
 };
 
+// Zero the entries of G and O (both ld x ld, O right after G) in rows or
+// columns c0.. that lie inside the leading m x m: the blocks a Gram of the
+// basis's new blocks then fills.
+__global__ void k_dav_zero(double *G, int ld, int m, int c0) {
+    for (int e = threadIdx.x; e < 2 * ld * ld; e += blockDim.x) {
+        const int i = (e / ld) % ld, j = e % ld;
+        if (i < m && j < m && (i >= c0 || j >= c0)) G[e] = 0.0;
+    }
+}
+
 // Cp = [I; -B] ((k + m) x k): W - V B = [W V] Cp
 __global__ void k_proj_coef_m(int k, int m, const double *B, double *Cp) {
     for (int e = threadIdx.x; e < (k + m) * k; e += blockDim.x) {
@@ -1060,8 +1070,10 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
     CK(dav_orth<T>(h, s, D, V, 0, V[0]));
     CK(spmm_T<T>(h, V[0], HV[0], k));
     int nb = 1, restarts = 0, since_best = 0, since_floor = 0;
+    int fresh = 0;   // leading blocks of the basis whose rows of G and O are current (float32 runs)
     double best = INFINITY, floor_best = INFINITY;
     std::vector<double> rho, theta;
+    const int ldg = D->nbmax * k;   // float32 runs keep G and O at this leading dimension
     while (true) {
         const int m = nb * k;
         GemmBlocks<T> av{}, ahv{};
@@ -1069,9 +1081,40 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
             av.p[q] = V[q];
             ahv.p[q] = HV[q];
         }
-        CK(launch_gram<T>(n, k, nb, av, nb, ahv, D->G, h->num_sms, h->stream, h->d_err));           // V^T HV
-        CK(launch_gram<T>(n, k, nb, av, nb, av, D->G + m * m, h->num_sms, h->stream, h->d_err));    // V^T V
-        CK(launch_rayleigh_ritz(m, k, m, D->G, D->G + m * m, m, nullptr, D->C, s->theta, s->status, h->stream));
+        bool incremental = false;
+        if constexpr (std::is_same<T, float>::value) {
+            // Only the blocks added since the last Rayleigh-Ritz step are new:
+            // for each, V_q^T HV_b and V_q^T V_b (q <= b) by one pair-Gram
+            // launch, mirrored into row b (the older blocks are unchanged).
+            const float *probe[2] = {V[0], HV[0]};
+            incremental = gram_pairs_fit(k, 2, probe, 2 * D->nbmax, 2 * D->nbmax * (k / 4) * (k / 4));
+            if (incremental) {
+                k_dav_zero<<<1, 256, 0, h->stream>>>(D->G, ldg, m, fresh * k);
+                CK(cudaGetLastError());
+                for (int b = fresh; b < nb; ++b) {
+                    const float *gb[8];   // V_0 .. V_b, HV_b
+                    for (int q = 0; q <= b; ++q) gb[q] = V[q];
+                    gb[b + 1] = HV[b];
+                    GramPair pr[12];
+                    int np = 0;
+                    for (int q = 0; q <= b; ++q) {
+                        const int fl = q < b ? GRAM_MIRROR : 0;
+                        pr[np++] = GramPair{q, b + 1, q, b, fl, b, q};                                // V_q^T HV_b
+                        pr[np++] = GramPair{q, b, D->nbmax + q, b, fl, D->nbmax + b, q};              // V_q^T V_b
+                    }
+                    CK(launch_gram_pairs(n, k, b + 2, gb, np, pr, D->G, ldg, 2 * ldg, false, h->d_err,
+                                         h->num_sms, h->stream));
+                }
+                fresh = nb;
+                CK(launch_rayleigh_ritz(m, k, m, D->G, D->G + ldg * ldg, ldg, nullptr, D->C, s->theta, s->status,
+                                        h->stream));
+            }
+        }
+        if (!incremental) {
+            CK(launch_gram<T>(n, k, nb, av, nb, ahv, D->G, h->num_sms, h->stream, h->d_err));           // V^T HV
+            CK(launch_gram<T>(n, k, nb, av, nb, av, D->G + m * m, h->num_sms, h->stream, h->d_err));    // V^T V
+            CK(launch_rayleigh_ritz(m, k, m, D->G, D->G + m * m, m, nullptr, D->C, s->theta, s->status, h->stream));
+        }
         CombineOut<T> ox{}, oh{};
         ox.z[0] = b.X; ox.C[0] = D->C; ox.c0[0] = 0; ox.norm_of = -1; ox.Cf = s->Cf;
         oh.z[0] = b.HX; oh.C[0] = D->C; oh.c0[0] = 0; oh.norm_of = -1; oh.Cf = s->Cf;
@@ -1114,6 +1157,7 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
             CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
             CK(cudaMemcpyAsync(HV[0], b.HW, blk, cudaMemcpyDeviceToDevice, h->stream));
             nb = 1;
+            fresh = 0;
             continue;
         }
         // a float32 run hands over once its residual stalls (15 iterations
@@ -1140,6 +1184,7 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
             CK(cudaMemcpyAsync(V[0], b.X, blk, cudaMemcpyDeviceToDevice, h->stream));
             CK(cudaMemcpyAsync(HV[0], b.HX, blk, cudaMemcpyDeviceToDevice, h->stream));
             nb = 1;
+            fresh = 0;
         }
         CK(cudaMemcpyAsync(V[nb], b.W, blk, cudaMemcpyDeviceToDevice, h->stream));
         CK(dav_orth<T>(h, s, D, V, nb, V[nb]));
