@@ -610,7 +610,9 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
             CK(cudaMemcpyAsync(b.HX, b.HW, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
             continue;
         }
-        // Stagnation (15 iterations without a 0.7x improvement), growth
+        // Stagnation (15 iterations without a 0.7x improvement, with a best
+        // below 1e-2: far above the float32 rounding floor more precision
+        // does not help a stalled run), growth
         // (4x above a best below 1e-3: at the float32 rounding floor the
         // HX/HP recurrences lose consistency and the residual grows
         // geometrically) or a floor (below 1e-2, no new minimum by 5 % in 3
@@ -629,7 +631,7 @@ cudaError_t run_phase(lobpcg_ctx *h, SolverState *s, int max_iters, bool stop_on
         if (worst < 0.7 * best) {
             best = worst;
             since_best = 0;
-        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best) ||
+        } else if (stop_on_stagnation && ((++since_best >= 15 && best < 1e-2) || (best < 1e-3 && worst > 4.0 * best) ||
                                           (floor_best < 1e-2 && since_floor >= 3))) {
             res.stagnated = true;
             if (snap) CK(cudaMemcpyAsync(b.X, snap, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream));
@@ -1161,8 +1163,9 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
             continue;
         }
         // a float32 run hands over once its residual stalls (15 iterations
-        // without a 0.7x gain), grows 4x above a best below 1e-3 or sits at
-        // a floor (below 1e-2, no new 5 % minimum in 3 iterations)
+        // without a 0.7x gain, best below 1e-2), grows 4x above a best below
+        // 1e-3 or sits at a floor (below 1e-2, no new 5 % minimum in 3
+        // iterations)
         if (worst < 0.95 * floor_best) {
             floor_best = worst;
             since_floor = 0;
@@ -1172,7 +1175,7 @@ cudaError_t dav_phase(lobpcg_ctx *h, SolverState *s, DavState *D, int max_iters,
         if (worst < 0.7 * best) {
             best = worst;
             since_best = 0;
-        } else if (stop_on_stagnation && (++since_best >= 15 || (best < 1e-3 && worst > 4.0 * best) ||
+        } else if (stop_on_stagnation && ((++since_best >= 15 && best < 1e-2) || (best < 1e-3 && worst > 4.0 * best) ||
                                           (floor_best < 1e-2 && since_floor >= 3))) {
             res.stagnated = true;
             break;
