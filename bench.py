@@ -322,6 +322,7 @@ def lobpcg_solves(pkg, A, p, stream, precs=("diag", "bjacobi", "fom", "fom_var",
             hist, used = h.precond_train(X0, harvest_iters=20, n_pairs=1 << 20, epochs=5, lr=1e-3)
             train = {"train_s": round(time.perf_counter() - t0, 3), "pairs": int(used),
                      "held_out_mse": [round(float(v), 5) for v in hist]}
+            train["apply"] = mlp_apply_report(h, A.n, p["k"], stream)
         def run_once(x0):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -378,6 +379,37 @@ def spmm_f64_report(pkg, A, p, stream, csr_bytes: int) -> dict:
     own = csr_bytes + 2 * n * k * 4
     return {"kernels": "k_split64, k_spmm_df_rows, k_spmm_df_cols (compensated float32)", "ms": round(ms, 3),
             "gbs_csr_equivalent_f64_vectors": round(own / (ms / 1e3) / 1e9, 1)}
+
+
+def mlp_apply_report(h, n: int, k: int, stream) -> dict:
+    """One learned-form application W = K_mlp^{-1} R on the n x k block
+    (precond_apply, mode "mlp": the fused kernel), median of 5 launches timed
+    with CUDA events on the handle's stream, R seeded N(0, 1).  Algorithmic
+    FLOPs: 2 (129 256 + 256 64) per (64-row tile, column) pair, against the
+    measured dense bf16 peak."""
+    import torch
+    pairs = (n + 63) // 64 * k
+    with torch.cuda.stream(stream):
+        g = torch.Generator(device="cuda").manual_seed(5)
+        R = torch.randn(n, k, device="cuda", dtype=torch.float32, generator=g)
+        W = torch.empty_like(R)
+        th = torch.linspace(-1.0, 1.0, k, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    h.precond_apply(R, th, W, mode="mlp")
+    ts = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.precond_apply(R, th, W, mode="mlp")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    tf = 2.0 * (129 * 256 + 256 * 64) * pairs / (ms / 1e3) / 1e12
+    peak = measured_peaks()["bf16_tflops"]
+    return {"kernel": "k_mlp_apply_fused", "pairs": int(pairs), "ms": round(ms, 4), "tflops": round(tf, 2),
+            "frac_of_bf16_peak": round(tf / peak, 4)}
 
 
 def mlp_kernels_report(pkg, stream, peak_tflops: float, rows: int = 500_000, batch: int = 4096) -> dict:

@@ -24,8 +24,7 @@ constexpr int MLP_NPARAM_CALLER = MLP_NHID * 129 + MLP_NHID + MLP_NOUT * MLP_NHI
 
 struct Mlp {
     float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;   // params, grads, Adam moments
-    float *ws = nullptr;          // inference workspace (inputs, hidden, outputs, scales)
-    int64_t cap_apply = 0;        // pairs the workspace holds
+    int64_t cap_apply = 0;        // (tile, column) pairs of one apply on the handle's block size
     float *Xp = nullptr, *Tp = nullptr;   // harvested pairs (inputs, targets)
     unsigned long long *d_count = nullptr;
     int64_t cap_pairs = 0;

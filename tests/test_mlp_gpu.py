@@ -120,11 +120,14 @@ def test_gradients_and_adam_match_oracle():
     h.destroy()
 
 
-def test_tile_apply_matches_oracle():
+@pytest.mark.parametrize("k", [8, 20])
+def test_tile_apply_matches_oracle(k):
+    """The fused apply kernel takes (tile, column) pairs in batches of 64:
+    at k = 8 a batch is 8 whole tiles, at k = 20 batches start and end
+    inside a tile's columns."""
     import torch
     pkg = _pkg()
     A = small_matrix()
-    k = 8
     h = handle(pkg, A, k=k)
     p = oracle_params(11)
     h.mlp_set_params(pack(p))
