@@ -178,13 +178,15 @@ __device__ __forceinline__ float diag_solve(float r, float d, double th) {
 
 // ------------------------------------------------------------------ fused apply
 
-// The whole apply W = D^{-1} R + c for batches of 64 (tile, column) pairs in
-// one kernel, the network's weights resident in shared memory as bf16 (one
-// CTA per SM): the pairs' inputs are built from R and d into shared memory,
+// The whole apply W = D^{-1} R + c in one kernel, in batches of 64 / k
+// whole tiles (at most 64 (tile, column) pairs), the network's weights
+// resident in shared memory as bf16 (one CTA per SM): a batch's rows of R
+// and d are read coalesced into shared memory, the pairs' inputs built there,
 // h = relu(W1 x + b1) and y = W2 h + b2 on the tensor cores (mma.sync
 // m16n8k16, FP32 accumulation, k-steps in ascending order as in
 // k_gemm_bf16, h rounded to bf16 after the bias and relu as k_gemm_bf16's
-// staging rounds it), and the outputs formed in place.  Nothing but R, d
+// staging rounds it), and the outputs formed in shared memory and written
+// back as the batch's contiguous rows of W (W may be R).  Nothing but R, d
 // and W leaves the SM (an unfused form through k_gemm_bf16 wrote the
 // inputs, a float32 hidden layer and the outputs to memory and read them
 // back: 2.5 ms per application at n = 2M, k = 16).
@@ -210,10 +212,11 @@ struct FaSmem {
         float y[FA_PAIRS][MLP_NOUT + 4];
     } xy;
     __nv_bfloat16 hb[FA_PAIRS][FA_HS];
-    float r[FA_PAIRS][MLP_TILE], d[FA_PAIRS][MLP_TILE];   // the pairs' residual and diagonal entries
+    float r[FA_PAIRS][MLP_TILE + 1];   // the pairs' residual entries, then their outputs (row stride 65: conflict-free)
+    float d[FA_PAIRS * MLP_TILE];      // the batch's diagonal entries
     float b1[MLP_NHID], b2[MLP_NOUT];
     float sc[FA_PAIRS];
-    double th[32];
+    float thf[32], thl[32];   // theta_j = thf + thl (+ 2^-48 |theta_j|), split once per CTA
 };
 
 __global__ void __launch_bounds__(FA_THREADS, 1) k_mlp_apply_fused(int64_t n, int k, const float *P, const float *R,
@@ -229,52 +232,62 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_mlp_apply_fused(int64_t n, in
         S.w2[e / MLP_NHID][e % MLP_NHID] = __float2bfloat16_rn(P[MLP_OFF_W2 + e]);
     for (int e = threadIdx.x; e < MLP_NHID; e += FA_THREADS) S.b1[e] = P[MLP_OFF_B1 + e];
     for (int e = threadIdx.x; e < MLP_NOUT; e += FA_THREADS) S.b2[e] = P[MLP_OFF_B2 + e];
-    for (int e = threadIdx.x; e < k; e += FA_THREADS) S.th[e] = theta[e];
-    const int64_t NP = ((n + MLP_TILE - 1) / MLP_TILE) * k;
-    const double ig = 1.0 / normG;
-    for (int64_t p0 = static_cast<int64_t>(blockIdx.x) * FA_PAIRS; p0 < NP;
-         p0 += static_cast<int64_t>(gridDim.x) * FA_PAIRS) {
+    for (int e = threadIdx.x; e < k; e += FA_THREADS) {
+        const float hi = __double2float_rn(theta[e]);
+        S.thf[e] = hi;
+        S.thl[e] = __double2float_rn(theta[e] - static_cast<double>(hi));
+    }
+    // float32 constants: GB300 runs FP64 (and conversions) at 1/64 of the
+    // FP32 rate, so nothing in the batch loop is float64
+    const float igf = static_cast<float>(1.0 / normG);
+    // A batch is T = 64 / k whole tiles (T k <= 64 pairs): its rows of R, d
+    // and W are contiguous, read and written with coalesced accesses.
+    const int T = FA_PAIRS / k;
+    const int64_t ntiles = (n + MLP_TILE - 1) / MLP_TILE;
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * T; t0 < ntiles; t0 += static_cast<int64_t>(gridDim.x) * T) {
+        const int tb = static_cast<int>(ntiles - t0 < T ? ntiles - t0 : T);
+        const int np = tb * k;                               // pairs q = tl k + j
+        const int64_t r0 = t0 * MLP_TILE;
+        const int rows = static_cast<int>(n - r0 < tb * MLP_TILE ? n - r0 : tb * MLP_TILE);
         __syncthreads();   // the previous batch is done with every buffer
-        // ---- inputs: the warp's pairs (a warp per pair, two rows per lane),
-        // every load issued before the first is used
-        {
-            float rv[FA_PPW][2], dv[FA_PPW][2];
+        for (int e = threadIdx.x; e < rows * k; e += FA_THREADS) {
+            const int row = e / k, j = e - row * k;
+            S.r[(row >> 6) * k + j][row & 63] = R[r0 * k + e];
+        }
+        for (int e = threadIdx.x; e < rows; e += FA_THREADS) S.d[e] = d[r0 + e];
+        __syncthreads();
+        // ---- inputs: the warp's pairs (a warp per pair, two rows per lane)
 #pragma unroll
-            for (int i = 0; i < FA_PPW; ++i) {
-                const int64_t p = p0 + warp * FA_PPW + i;
-                const int64_t t = p / k;
-                const int j = static_cast<int>(p % k);
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int64_t row = t * MLP_TILE + lane + 32 * hh;
-                    const bool ok = p < NP && row < n;
-                    rv[i][hh] = ok ? R[row * k + j] : 0.f;
-                    dv[i][hh] = ok ? d[row] : 0.f;
-                }
+        for (int i = 0; i < FA_PPW; ++i) {
+            const int q = warp * FA_PPW + i;
+            if (q >= np) {
+                for (int c = lane; c < MLP_KIN; c += 32) S.xy.x[q][c] = __float2bfloat16_rn(0.f);
+                if (lane == 0) S.sc[q] = 0.f;
+                continue;
             }
+            const int tl = q / k, j = q - tl * k;
+            float rv[2], dv[2];
 #pragma unroll
-            for (int i = 0; i < FA_PPW; ++i) {
-                const int q = warp * FA_PPW + i;
-                const int64_t p = p0 + q;
-                float ss = rv[i][0] * rv[i][0] + rv[i][1] * rv[i][1];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-                const float sv = sqrtf(ss);
-                const float is = sv > 0.f ? 1.f / sv : 0.f;
-                const float th = p < NP ? static_cast<float>(S.th[p % k]) : 0.f;
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    S.r[q][lane + 32 * hh] = rv[i][hh];
-                    S.d[q][lane + 32 * hh] = dv[i][hh];
-                    S.xy.x[q][lane + 32 * hh] = __float2bfloat16_rn(rv[i][hh] * is);
-                    S.xy.x[q][MLP_TILE + lane + 32 * hh] =
-                        __float2bfloat16_rn(p < NP ? static_cast<float>((dv[i][hh] - th) * ig) : 0.f);
-                }
-                if (lane < MLP_KIN - 2 * MLP_TILE)
-                    S.xy.x[q][2 * MLP_TILE + lane] =
-                        __float2bfloat16_rn((lane == 0 && p < NP) ? static_cast<float>(th * ig) : 0.f);
-                if (lane == 0) S.sc[q] = sv;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int rl = lane + 32 * hh;
+                const bool ok = tl * MLP_TILE + rl < rows;
+                rv[hh] = ok ? S.r[q][rl] : 0.f;
+                dv[hh] = ok ? S.d[tl * MLP_TILE + rl] : 0.f;
             }
+            float ss = rv[0] * rv[0] + rv[1] * rv[1];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float sv = sqrtf(ss);
+            const float is = sv > 0.f ? 1.f / sv : 0.f;
+            const float th = S.thf[j];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                S.xy.x[q][lane + 32 * hh] = __float2bfloat16_rn(rv[hh] * is);
+                S.xy.x[q][MLP_TILE + lane + 32 * hh] = __float2bfloat16_rn((dv[hh] - th) * igf);
+            }
+            if (lane < MLP_KIN - 2 * MLP_TILE)
+                S.xy.x[q][2 * MLP_TILE + lane] = __float2bfloat16_rn((lane == 0) ? th * igf : 0.f);
+            if (lane == 0) S.sc[q] = sv;
         }
         __syncthreads();
         // ---- h = relu(W1 x + b1): warp w, hidden units [16 w, 16 w + 16)
@@ -353,27 +366,29 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_mlp_apply_fused(int64_t n, in
                 }
         }
         __syncthreads();
-        // ---- outputs, the warp's pairs (R and d from shared memory)
+        // ---- outputs, the warp's pairs, into S.r over their residuals
 #pragma unroll
         for (int i = 0; i < FA_PPW; ++i) {
             const int q = warp * FA_PPW + i;
-            const int64_t p = p0 + q;
-            if (p >= NP) break;
-            const int64_t t = p / k;
-            const int j = static_cast<int>(p % k);
-            const double thj = S.th[j];
-            const float f = static_cast<float>(S.sc[q] / normG);
+            if (q >= np) break;
+            const int tl = q / k, j = q - tl * k;
+            const float thf = S.thf[j], thl = S.thl[j];
+            const float delta = 1e-3f * fmaxf(1.f, fabsf(thf));
+            const float f = S.sc[q] * igf;
             float c[2], wd[2];
             float cc = 0.f, dd = 0.f;
             bool finite = true;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
-                const int64_t row = t * MLP_TILE + lane + 32 * hh;
+                const int rl = lane + 32 * hh;
                 c[hh] = 0.f;
                 wd[hh] = 0.f;
-                if (row < n) {
-                    c[hh] = f * S.xy.y[q][lane + 32 * hh];
-                    wd[hh] = diag_solve(S.r[q][lane + 32 * hh], S.d[q][lane + 32 * hh], thj);
+                if (tl * MLP_TILE + rl < rows) {
+                    c[hh] = f * S.xy.y[q][rl];
+                    // the guarded shifted pivot g(d - theta_j), the shift in two float steps
+                    const float t = __fsub_rn(__fsub_rn(S.d[tl * MLP_TILE + rl], thf), thl);
+                    const float gp = (t >= 0.f) ? fmaxf(t, delta) : -fmaxf(-t, delta);
+                    wd[hh] = S.r[q][rl] / gp;
                     finite = finite && isfinite(c[hh]);
                     cc += c[hh] * c[hh];
                     dd += wd[hh] * wd[hh];
@@ -388,9 +403,14 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_mlp_apply_fused(int64_t n, in
             const float scale = !finite ? 0.f : (cc > dd ? sqrtf(dd / cc) : 1.f);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
-                const int64_t row = t * MLP_TILE + lane + 32 * hh;
-                if (row < n) W[row * k + j] = finite ? wd[hh] + scale * c[hh] : wd[hh];
+                const int rl = lane + 32 * hh;
+                if (tl * MLP_TILE + rl < rows) S.r[q][rl] = finite ? wd[hh] + scale * c[hh] : wd[hh];
             }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * k; e += FA_THREADS) {
+            const int row = e / k, j = e - row * k;
+            W[r0 * k + e] = S.r[(row >> 6) * k + j][row & 63];
         }
     }
 }
@@ -728,7 +748,8 @@ cudaError_t mlp_apply(lobpcg_ctx *h, int k, const float *R, const double *theta,
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int64_t batches = (P + FA_PAIRS - 1) / FA_PAIRS;
+    const int64_t ntiles = (n + MLP_TILE - 1) / MLP_TILE, T = FA_PAIRS / k;
+    const int64_t batches = (ntiles + T - 1) / T;
     const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches, h->num_sms)));
     k_mlp_apply_fused<<<blocks, FA_THREADS, sizeof(FaSmem), s>>>(n, k, M.P, R, h->T.diag, theta, h->gershgorin, W);
     return cudaGetLastError();
