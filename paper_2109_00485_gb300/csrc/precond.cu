@@ -26,15 +26,41 @@ __device__ __forceinline__ double guard_shift(double t, double theta) {
     return s * fmax(fabs(t), delta);
 }
 
+// The same guarded pivot in float32 for float32 blocks, theta_j given as two
+// floats (hi + lo, split once per CTA): t = (v - hi) - lo.  GB300 runs FP64
+// arithmetic and conversions at 1/64 of its FP32 rate, so a float64 division
+// per element cost more than the rest of an apply.
+__device__ __forceinline__ float guard_shift_f(float v, float thh, float thl) {
+    const float t = __fsub_rn(__fsub_rn(v, thh), thl);
+    const float delta = 1e-3f * fmaxf(1.f, fabsf(thh));
+    return (t >= 0.f) ? fmaxf(t, delta) : -fmaxf(-t, delta);
+}
+
+// theta (k <= 32 doubles) split into float pairs in shared memory
+__device__ __forceinline__ void split_theta(const double *theta, int k, float *thh, float *thl) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const float hi = __double2float_rn(theta[j]);
+        thh[j] = hi;
+        thl[j] = __double2float_rn(theta[j] - static_cast<double>(hi));
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void k_precond_diag(int64_t n, int k, const T *R, const double *theta, const float *d, T *W) {
+    __shared__ float thh[32], thl[32];
+    if constexpr (std::is_same<T, float>::value) split_theta(theta, k, thh, thl);
     const int64_t total = n * k;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t i = e / k;
-        const int j = static_cast<int>(e % k);
-        const double th = theta[j];
-        W[e] = static_cast<T>(static_cast<double>(R[e]) / guard_shift(static_cast<double>(d[i]) - th, th));
+        const int j = static_cast<int>(e - i * k);
+        if constexpr (std::is_same<T, float>::value) {
+            W[e] = R[e] / guard_shift_f(d[i], thh[j], thl[j]);
+        } else {
+            const double th = theta[j];
+            W[e] = static_cast<T>(static_cast<double>(R[e]) / guard_shift(static_cast<double>(d[i]) - th, th));
+        }
     }
 }
 
@@ -154,6 +180,8 @@ __global__ void __launch_bounds__(256) k_bjacobi_apply(int64_t n, int k, const f
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * BJ;
     const int m = static_cast<int>(n - t0 < BJ ? n - t0 : BJ);
     const float *Qt = Q + static_cast<int64_t>(blockIdx.x) * BJ * BJ;
+    __shared__ float thh[32], thl[32];
+    if constexpr (std::is_same<T, float>::value) split_theta(theta, k, thh, thl);
     for (int e = threadIdx.x; e < BJ * BJ / 4; e += blockDim.x)
         reinterpret_cast<float4 *>(sQ)[e] = reinterpret_cast<const float4 *>(Qt)[e];
     for (int e = threadIdx.x; e < BJ * k; e += blockDim.x) {
@@ -165,8 +193,12 @@ __global__ void __launch_bounds__(256) k_bjacobi_apply(int64_t n, int k, const f
         const int l = e / k, j = e % k;
         float s = 0.f;
         for (int r = 0; r < BJ; ++r) s = fmaf(sQ[r * BJ + l], sR[r * k + j], s);
-        const double th = theta[j];
-        sZ[e] = static_cast<float>(s / guard_shift(static_cast<double>(lam[t0 + l]) - th, th));
+        if constexpr (std::is_same<T, float>::value) {
+            sZ[e] = s / guard_shift_f(lam[t0 + l], thh[j], thl[j]);
+        } else {
+            const double th = theta[j];
+            sZ[e] = static_cast<float>(s / guard_shift(static_cast<double>(lam[t0 + l]) - th, th));
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
