@@ -114,68 +114,6 @@ __device__ __forceinline__ void tri_rc(int e, int &r, int &c) {
     c = e - q * (q - 1) / 2;
 }
 
-// In-place Cholesky of the m x m matrix A (lower triangle used), row-major in
-// shared memory: A = L L^T, L in the lower triangle, upper triangle zeroed.
-// Right-looking; the pivot reciprocal 1/L_jj goes to rd[j].  Returns false if
-// a pivot is not > 0 or the pivots span more than `span` (max L_jj / min L_jj).
-__device__ bool cta_cholesky(double *A, int m, double span, double *rd) {
-    __shared__ int ok;
-    __shared__ double dmin, dmax, rl;
-    if (threadIdx.x == 0) { ok = 1; dmin = 1e300; dmax = 0.0; }
-    __syncthreads();
-    for (int j = 0; j < m; ++j) {
-        if (threadIdx.x == 0) {
-            const double sj = A[j * m + j];
-            if (!(sj > 0.0)) {
-                ok = 0;
-            } else {
-                const double r = rsqrt64(sj);
-                const double l = sj * r;
-                A[j * m + j] = l;
-                rl = r;
-                rd[j] = r;
-                dmin = fmin(dmin, l);
-                dmax = fmax(dmax, l);
-            }
-        }
-        __syncthreads();
-        if (!ok) return false;
-        const double r = rl;
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] *= r;
-        __syncthreads();
-        // trailing lower triangle including its diagonal: pairs (i, l), j < l <= i
-        const int nt = m - j - 1;
-        const int cnt = nt * (nt + 1) / 2;
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            int r1, c1;
-            tri_rc(e, r1, c1);            // strictly lower pairs of an (nt + 1) triangle
-            const int i = j + r1, l = j + 1 + c1;
-            A[i * m + l] -= A[i * m + j] * A[l * m + j];
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, jj = e % m;
-        if (jj > i) A[e] = 0.0;
-    }
-    __syncthreads();
-    return dmax <= span * dmin;
-}
-
-// Li = L^{-1} for lower-triangular L (m x m, shared memory), rd[i] = 1/L_ii:
-// column j by forward substitution, one thread per column.
-__device__ void cta_tri_inverse(const double *L, const double *rd, double *Li, int m) {
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        for (int i = 0; i < m; ++i) {
-            if (i < j) { Li[i * m + j] = 0.0; continue; }
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int p = j; p < i; ++p) s -= L[i * m + p] * Li[p * m + j];
-            Li[i * m + j] = s * rd[i];
-        }
-    }
-    __syncthreads();
-}
-
 // C = A B (m x m, shared), optionally with A or B transposed.
 __device__ void cta_matmul(const double *A, bool ta, const double *B, bool tb, double *Cm, int m) {
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
@@ -1131,8 +1069,11 @@ __global__ void k_orth_factor(int k, const double *B, double *Tout, int *status)
         __syncthreads();
     };
     load();
-    if (cta_cholesky(sB, k, 1e7, rdk)) {
-        cta_tri_inverse(sB, rdk, sL, k);   // sL = L^{-1}
+    if (cta_cholesky_rr(sB, k, 1e7, rdk)) {
+        // sL = L^{-1}: the forward solve of the Rayleigh-Ritz step on I
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) sL[e] = (e / k == e % k) ? 1.0 : 0.0;
+        __syncthreads();
+        cta_trsm_fwd_rr(sB, rdk, sL, k, k);
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const int i = e / k, j = e % k;
             Tout[e] = dsc[i] * sL[j * k + i];
