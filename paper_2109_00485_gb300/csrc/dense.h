@@ -81,9 +81,15 @@ cudaError_t launch_gram_x_df(int64_t n, int k, const double *X, const double *HX
 // HX <- HX C + HP (float64; X32, HX32 float32 copies), then R32 = HX - X
 // Theta, W = R32 (mode 0) or the diagonal-preconditioned R32 (mode 1), and
 // norms (zeroed first) = (||r_j||^2, ||x_j||^2), as launch_resid_mixed.
-cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, const float *P,
-                               const float *HP, float *X32, float *HX32, const double *theta, const float *d,
-                               float *W, float *R32, int mode, double *norms, int num_sms, cudaStream_t s);
+// With C23 (float64 nz k x k: the W and P rows of the Ritz coefficients),
+// Wb, HWb (the basis blocks W, HW) and colsq: P <- [W P] C23 and HP <- [HW HP]
+// C23 in place first (float32; nz = 1 leaves the P block out), colsq =
+// ||p_j||^2 (zeroed first); the X and HX updates then add these.
+cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, float *P, float *HP,
+                               float *X32, float *HX32, const double *theta, const float *d, float *W, float *R32,
+                               int mode, double *norms, int num_sms, cudaStream_t s, const float *Wb = nullptr,
+                               const float *HWb = nullptr, const double *C23 = nullptr, int nz = 0,
+                               double *colsq = nullptr);
 bool combine_ff_ok(int k, int na, const float *const *blocks, const float *Z);
 cudaError_t launch_combine_ff(int64_t n, int k, int na, const float *const *A, const double *C, float *Z, int *err,
                               int num_sms, cudaStream_t s);

@@ -32,17 +32,30 @@ constexpr int XU_THREADS = 256;
 //   ||x_j||^2).  The updated X and HX enter the residual as float pairs, so
 //   HX - X Theta is formed without cancellation loss: TwoSum of hx_hi and
 //   -fl(x_hi theta_hi), the rest in the low word.
+// With C23 (float64, nz k x k: the W and P rows of the Ritz coefficients)
+// the new search directions are formed here too, in float32 from the staged
+// rows: P <- [W P] C23, HP <- [HW HP] C23 (P and HP in place, the P block
+// left out when nz = 1), colsq += ||p_j||^2; W, the basis block, is read
+// before the new W is written over it.
 __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C,
-                                                            const float *P, const float *HP, float *X32, float *HX32,
+                                                            float *P, float *HP, float *X32, float *HX32,
                                                             const double *theta, const float *d, float *W, float *R32,
-                                                            int mode, double *norms) {
+                                                            int mode, double *norms, const float *Wb,
+                                                            const float *HWb, const double *C23, int nz,
+                                                            double *colsq) {
     // C's words as duplicated pairs (c, c), (-c, -c), (c_lo, c_lo) (k x k
     // each); a row element of X and HX as the pairs (x_hi, hx_hi), (x_lo,
     // hx_lo) (per x k each): one packed df_mac2 updates x and hx together
     extern __shared__ float2 xs2[];
-    __shared__ double red[64];      // [2k]
+    __shared__ double red[96];      // [3k]
     const int per = XU_THREADS / k;
     float2 *cp = xs2, *cn = xs2 + k * k, *cl = xs2 + 2 * k * k, *zh = xs2 + 3 * k * k, *zl = zh + per * k;
+    // the fused directions: the pass's rows of W, P, HW, HP, and C23 in float32
+    float *wr = reinterpret_cast<float *>(zl + per * k), *pr = wr + per * k, *hwr = pr + per * k,
+          *hpr = hwr + per * k, *c23 = hpr + per * k;
+    const bool fuse = C23 != nullptr;
+    if (fuse)
+        for (int q = threadIdx.x; q < nz * k * k; q += blockDim.x) c23[q] = __double2float_rn(C23[q]);
     for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
         float a, b;
         df_split(C[q], a, b);
@@ -50,7 +63,7 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
         cn[q] = make_float2(-a, -a);
         cl[q] = make_float2(b, b);
     }
-    for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) red[q] = 0.0;
+    for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) red[q] = 0.0;
     const int r = threadIdx.x / k, j = threadIdx.x % k;
     const bool active = r < per;
     float th_h = 0.f, th_l = 0.f;
@@ -60,19 +73,25 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
     // float32 sums of nonnegative terms over this thread's rows (a few
     // hundred at most: relative error below 1e-4, enough for the norms'
     // use in the convergence test), folded into float64 once at the end
-    float rr = 0.f, xx = 0.f;
+    float rr = 0.f, xx = 0.f, pp = 0.f;
     // a pass's inputs are loaded during the pass before (thread r k + j
     // loads element (r, j) of X and HX, which it also updates)
     const int64_t step = static_cast<int64_t>(gridDim.x) * per;
     double fx = 0.0, fh = 0.0;
-    float fp = 0.f, fhp = 0.f, fd = 0.f;
+    float fp = 0.f, fhp = 0.f, fd = 0.f, fw = 0.f, fhw = 0.f;
     auto fetch = [&](int64_t i) {
         const int rws = static_cast<int>(n - i < per ? n - i : per);
         if (threadIdx.x < rws * k) {
             fx = X[i * k + threadIdx.x];
             fh = HX[i * k + threadIdx.x];
-            fp = P[i * k + threadIdx.x];
-            fhp = HP[i * k + threadIdx.x];
+            if (!fuse || nz == 2) {
+                fp = P[i * k + threadIdx.x];
+                fhp = HP[i * k + threadIdx.x];
+            }
+            if (fuse) {
+                fw = Wb[i * k + threadIdx.x];
+                fhw = HWb[i * k + threadIdx.x];
+            }
             if (mode == 1) fd = d[i + r];
         }
     };
@@ -87,6 +106,12 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
             df_split(fh, c, e);
             zh[threadIdx.x] = make_float2(a, c);
             zl[threadIdx.x] = make_float2(b, e);
+            if (fuse) {
+                wr[threadIdx.x] = fw;
+                hwr[threadIdx.x] = fhw;
+                pr[threadIdx.x] = fp;
+                hpr[threadIdx.x] = fhp;
+            }
         }
         __syncthreads();
         if (i0 + step < n) fetch(i0 + step);
@@ -96,6 +121,26 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
                 df_mac2(zh[r * k + l], zl[r * k + l], cp[l * k + j], cn[l * k + j], cl[l * k + j], s2, c2);
             const float sx = s2.x, cx = c2.x, sh = s2.y, chh = c2.y;
             const int64_t e = (i0 + r) * k + j;
+            float pn = pe, hpn = hpe;
+            if (fuse) {   // P = [W P] C23, HP = [HW HP] C23
+                float a = 0.f, b = 0.f;
+                for (int l = 0; l < k; ++l) {
+                    const float c = c23[l * k + j];
+                    a = __fmaf_rn(wr[r * k + l], c, a);
+                    b = __fmaf_rn(hwr[r * k + l], c, b);
+                }
+                if (nz == 2)
+                    for (int l = 0; l < k; ++l) {
+                        const float c = c23[(k + l) * k + j];
+                        a = __fmaf_rn(pr[r * k + l], c, a);
+                        b = __fmaf_rn(hpr[r * k + l], c, b);
+                    }
+                pn = a;
+                hpn = b;
+                P[e] = a;
+                HP[e] = b;
+                pp = __fmaf_rn(a, a, pp);
+            }
             // + P, + HP: TwoSum with the high word, the rest into the low word
             auto add = [](float s, float c, float a, float &u, float &v) {
                 u = __fadd_rn(s, a);
@@ -103,8 +148,8 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
                 v = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, ba)), __fsub_rn(a, ba)), c);
             };
             float ux, vx, uh, vh;
-            add(sx, cx, pe, ux, vx);
-            add(sh, chh, hpe, uh, vh);
+            add(sx, cx, pn, ux, vx);
+            add(sh, chh, hpn, uh, vh);
             X[e] = df_to_f64(ux) + df_to_f64(vx);
             HX[e] = df_to_f64(uh) + df_to_f64(vh);
             const float x32 = __fadd_rn(ux, vx);
@@ -132,9 +177,12 @@ __global__ void __launch_bounds__(XU_THREADS) k_xupdate2_df(int64_t n, int k, do
     if (active) {
         atomicAdd(&red[j], static_cast<double>(rr));
         atomicAdd(&red[k + j], static_cast<double>(xx));
+        atomicAdd(&red[2 * k + j], static_cast<double>(pp));
     }
     __syncthreads();
     for (int q = threadIdx.x; q < 2 * k; q += blockDim.x) atomicAdd(&norms[q], red[q]);
+    if (fuse)
+        for (int q = threadIdx.x; q < k; q += blockDim.x) atomicAdd(&colsq[q], red[2 * k + q]);
 }
 
 constexpr int GX_THREADS = 256;
@@ -262,17 +310,20 @@ __global__ void __launch_bounds__(GX_THREADS) k_gram_x_df(int64_t n, int k, cons
 
 bool mixed_df_ok(int k) { return k >= 1 && k <= 32; }
 
-cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, const float *P,
-                               const float *HP, float *X32, float *HX32, const double *theta, const float *d,
-                               float *W, float *R32, int mode, double *norms, int num_sms, cudaStream_t s) {
-    if (!mixed_df_ok(k)) return cudaErrorInvalidValue;
+cudaError_t launch_xupdate2_df(int64_t n, int k, double *X, double *HX, const double *C, float *P, float *HP,
+                               float *X32, float *HX32, const double *theta, const float *d, float *W, float *R32,
+                               int mode, double *norms, int num_sms, cudaStream_t s, const float *Wb,
+                               const float *HWb, const double *C23, int nz, double *colsq) {
+    if (!mixed_df_ok(k) || (C23 && (nz < 1 || nz > 2 || !Wb || !HWb || !colsq))) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * k, s);
+    if (e == cudaSuccess && C23) e = cudaMemsetAsync(colsq, 0, sizeof(double) * k, s);
     if (e != cudaSuccess) return e;
     const int per = XU_THREADS / k;
-    const size_t smem = sizeof(float2) * (3 * k * k + 2 * per * k);
+    const size_t smem = sizeof(float2) * (3 * k * k + 2 * per * k) + sizeof(float) * (4 * per * k + 2 * k * k);
     int blocks = static_cast<int>(std::min<int64_t>((n + per - 1) / per, static_cast<int64_t>(num_sms) * 8));
     if (blocks < 1) blocks = 1;
-    k_xupdate2_df<<<blocks, XU_THREADS, smem, s>>>(n, k, X, HX, C, P, HP, X32, HX32, theta, d, W, R32, mode, norms);
+    k_xupdate2_df<<<blocks, XU_THREADS, smem, s>>>(n, k, X, HX, C, P, HP, X32, HX32, theta, d, W, R32, mode, norms,
+                                                   Wb, HWb, C23, nz, colsq);
     return cudaGetLastError();
 }
 

@@ -797,22 +797,25 @@ cudaError_t run_phase_mixed(lobpcg_ctx *h, SolverState *s, int max_iters, PhaseR
                                 s->status, h->stream));
         // P = [W P] C_23 (with ||p_j||^2), HP = [HW HP] C_23, then
         // X = X C_x + P, HX = HX C_x + HP in float64
-        GemmBlocks<float> aWP{}, aHWP{};
-        aWP.p[0] = f.W; aWP.p[1] = f.P;
-        aHWP.p[0] = f.HW; aHWP.p[1] = f.HP;
-        CombineOut<float> op{}, ohp{};
-        op.Cf = s->Cf;
-        ohp.Cf = s->Cf;
-        op.z[0] = f.P; op.C[0] = s->C + static_cast<int64_t>(k) * k; op.c0[0] = 0; op.norm_of = 0;
-        ohp.z[0] = f.HP; ohp.C[0] = s->C + static_cast<int64_t>(k) * k; ohp.c0[0] = 0; ohp.norm_of = -1;
-        CK(launch_combine<float>(n, k, na - 1, aWP, 1, op, s->colsqP, h->num_sms, h->stream));
-        CK(launch_combine<float>(n, k, na - 1, aHWP, 1, ohp, nullptr, h->num_sms, h->stream));
+        const double *C23 = s->C + static_cast<int64_t>(k) * k;
         if (mixed_df_ok(k)) {
-            // both updates and the next iteration's residual in one pass
+            // the directions, both updates and the next iteration's residual
+            // in one pass
             CK(launch_xupdate2_df(n, k, d.X, d.HX, s->C, f.P, f.HP, f.X, f.HX, s->theta, h->T.diag, f.W, R32,
-                                  pmode == 1 ? 1 : 0, s->norms, h->num_sms, h->stream));
+                                  pmode == 1 ? 1 : 0, s->norms, h->num_sms, h->stream, f.W, f.HW, C23, na - 1,
+                                  s->colsqP));
             resid_ready = true;
         } else {
+            GemmBlocks<float> aWP{}, aHWP{};
+            aWP.p[0] = f.W; aWP.p[1] = f.P;
+            aHWP.p[0] = f.HW; aHWP.p[1] = f.HP;
+            CombineOut<float> op{}, ohp{};
+            op.Cf = s->Cf;
+            ohp.Cf = s->Cf;
+            op.z[0] = f.P; op.C[0] = C23; op.c0[0] = 0; op.norm_of = 0;
+            ohp.z[0] = f.HP; ohp.C[0] = C23; ohp.c0[0] = 0; ohp.norm_of = -1;
+            CK(launch_combine<float>(n, k, na - 1, aWP, 1, op, s->colsqP, h->num_sms, h->stream));
+            CK(launch_combine<float>(n, k, na - 1, aHWP, 1, ohp, nullptr, h->num_sms, h->stream));
             CK(launch_xupdate(n, k, d.X, s->C, f.P, f.X, h->num_sms, h->stream));
             CK(launch_xupdate(n, k, d.HX, s->C, f.HP, f.HX, h->num_sms, h->stream));
         }
